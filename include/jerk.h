@@ -1,0 +1,185 @@
+/*
+ * jerk.h -- C ABI of the GB300 (sm_103a) Fourier-domain jerk search.
+ *
+ * The method (Adamek, Novotny, Dimoudi & Armour, "Searching for pulsars in
+ * extreme orbits - GPU acceleration of the Fourier domain 'jerk' search"):
+ * a power-normalised complex spectrum is correlated, by overlap-and-save
+ * (Fig. 1), with one matched filter per (z, w), z = fdot T^2 and
+ * w = fddot T^3 (Sec. 2); the |.|^2 power plane over (r, z, w) is harmonic-
+ * summed and thresholded peaks are kept as candidates after computing the
+ * mean and standard deviation (Sec. 3).
+ *
+ * Conventions used throughout:
+ *   b        Fourier cells per bin ("numbetween"), must be 2.
+ *   N        complex bins of the input spectrum; cells p = 0 .. bN-1, r = p/b.
+ *   z_i      -zmax + i dz, i < nz = 2 zmax/dz + 1.
+ *   w_j      -wmax + j dw, j < nw = 2 wmax/dw + 1.
+ *   t        template index j*nz + i.
+ *   m(z,w)   ceil(|z|/2 + |w|/8) + pad_bins: template half-width in bins.
+ *   M        max over the bank of m(z, w); K = 2 b M + 1 taps.
+ *   L        segment (FFT) length in cells; V = L - K + 1 outputs kept per segment.
+ *   stage H  S_H(p, z, w) = sum_{h=1..H} P(h p, h z, h w), defined where
+ *            H p < bN, |H z| <= zmax and |H w| <= wmax.
+ *
+ * Memory: every pointer argument named d_* is DEVICE memory on the plan's
+ * device; h_* is host memory.  "complex64" is interleaved (re, im) float32.
+ * The plan owns its device buffers (template bank, workspace, candidates);
+ * the caller owns every buffer it passes in.  Calls taking a stream enqueue
+ * work on that cudaStream_t (NULL = legacy default stream) and return
+ * before it completes, unless stated otherwise.
+ *
+ * Errors: no call aborts or throws.  Invalid arguments return JERK_EINVAL
+ * with nothing enqueued; a CUDA error (including a sticky one from earlier
+ * work) returns JERK_ECUDA; allocation failures return JERK_ENOMEM.  A plan
+ * is not thread-safe; distinct plans are independent.
+ */
+#ifndef JERK_H_
+#define JERK_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct jerk_plan_s *jerk_plan;
+
+typedef enum {
+    JERK_OK = 0,
+    JERK_EINVAL = 1,     /* invalid argument or parameter set */
+    JERK_ENOMEM = 2,     /* device or host allocation failed / does not fit */
+    JERK_ECUDA = 3,      /* a CUDA runtime error */
+    JERK_ETIMEOUT = 4,   /* a bounded device-side wait expired */
+    JERK_EOVERFLOW = 5,  /* more candidates than the buffer holds */
+    JERK_ESTATE = 6      /* call out of order (e.g. search before templates) */
+} jerk_status;
+
+enum { JERK_THRESH_ABS = 0, JERK_THRESH_SIGMA = 1 };
+enum { JERK_MAX_STAGES = 4, JERK_MAX_HARMONIC = 8 };
+
+/* Search parameters.  Sec. 2 defines the (z, w) filters; Sec. 3 the
+ * user threshold, statistics and harmonic sum. */
+typedef struct {
+    int32_t zmax, dz;        /* zmax % dz == 0, dz > 0, zmax >= 0 */
+    int32_t wmax, dw;        /* wmax % dw == 0, dw > 0, wmax >= 0 */
+    int32_t numbetween;      /* b; must be 2 */
+    int32_t pad_bins;        /* P >= 1; default 16 */
+    int32_t seg_len;         /* L in cells: 1024, 2048, 4096 or 8192; 0 = choose */
+    int32_t n_stages;        /* 1..4 */
+    int32_t stages[4];       /* strictly ascending, stages[0] == 1, each <= 8 */
+    int32_t thresh_mode;     /* JERK_THRESH_ABS or JERK_THRESH_SIGMA */
+    float   thresh[4];       /* ABS: power; SIGMA: T in theta = mu + T sigma */
+    int32_t norm_block;      /* B in bins (1..4096), 0 = input already normalised */
+    int32_t precision;       /* 0 = FP32 (the only value accepted) */
+    int64_t max_bins;        /* capacity: largest N a search may use */
+    int64_t max_candidates;  /* capacity of the plan's candidate buffer */
+} jerk_params;
+
+/* One candidate: a peak of the stage-H max-projection over (z, w). */
+typedef struct {
+    int64_t p;               /* cell index; Fourier frequency r = p / b */
+    double  r;
+    int32_t t;               /* template index of the maximum (lowest t on ties) */
+    int32_t z_idx, w_idx;    /* t = w_idx * nz + z_idx */
+    int32_t stage;           /* H */
+    float   z, w;            /* z_i, w_j of the fundamental */
+    float   power;           /* S_H at (p, t) in normalised power units (FP32) */
+    int32_t reserved;
+} jerk_candidate;
+
+/* Read-only description of a plan (sizes derived from the parameters). */
+typedef struct {
+    int32_t nz, nw, n_templates;
+    int32_t bank_halfwidth;  /* M in bins */
+    int32_t taps;            /* K = 2 b M + 1 */
+    int32_t seg_len;         /* L */
+    int32_t seg_valid;       /* V = L - K + 1 */
+    int32_t device;
+    int64_t max_bins;
+    int64_t slot_floats;     /* harmonic-row workspace at max_bins, in floats */
+    int64_t workspace_bytes; /* device bytes the plan holds */
+    const void *d_bank;      /* complex64[n_templates][L] template spectra (valid after jerk_templates) */
+} jerk_info;
+
+/* Validate `params`, select device `device` (made current), size and
+ * allocate the plan's device memory for spectra of up to max_bins bins.
+ * The template bank is not built yet: call jerk_templates next.
+ * On error *out is set to NULL. */
+jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *out);
+
+/* Build the template bank: for every (z, w), the taps
+ *   c_d = conj(rho(d/b; z, w)),  |d| <= b m(z, w),
+ *   rho(q; z, w) = int_{-1/2}^{1/2} exp(2 pi i (-q u + z u^2/2 + w u^3/6)) du
+ * (the Fourier response of a signal with constant fddot, Sec. 2; u is time
+ * from mid-observation) by FP64 Gauss-Legendre quadrature on the GPU, then
+ * their length-L spectra (FP64 FFT, stored FP32, 1/L folded in).  Enqueued
+ * on `stream`; the plan may be searched once it completes. */
+jerk_status jerk_templates(jerk_plan plan, void *stream);
+
+/* The whole hot path for one spectrum d_spec (complex64[n], device,
+ * 1 <= n <= max_bins), enqueued on `stream`, no host synchronisation:
+ * normalise (if norm_block > 0) -> segment FFT -> template multiply ->
+ * inverse FFT -> |.|^2 (overlap-and-save, Fig. 1) -> statistics (SIGMA
+ * mode) and stage-1 max-projection -> harmonic sums -> thresholded peaks
+ * (Sec. 3) into the plan's candidate buffer.  d_spec must stay valid until
+ * the stream reaches the end of this work.  Returns JERK_ESTATE before
+ * jerk_templates. */
+jerk_status jerk_search(jerk_plan plan, const void *d_spec, int64_t n, void *stream);
+
+/* As jerk_search, with h_spec in host memory (pageable or pinned): the
+ * spectrum is copied into a plan-owned device buffer on `stream` first. */
+jerk_status jerk_search_host(jerk_plan plan, const void *h_spec, int64_t n, void *stream);
+
+/* Wait for the last search to finish and copy its candidates to h_out
+ * (capacity cap records), sorted by (stage position, p).  *n_out receives
+ * the number found.  If it exceeds cap (JERK_EOVERFLOW, first cap records
+ * copied) or the plan's max_candidates (JERK_EOVERFLOW, the kept ones are
+ * not guaranteed to be the first), the call says so. */
+jerk_status jerk_candidates(jerk_plan plan, jerk_candidate *h_out, int64_t cap, int64_t *n_out);
+
+/* Release everything the plan owns.  NULL is accepted. */
+jerk_status jerk_plan_destroy(jerk_plan plan);
+
+/* Static, human-readable name of a status code. */
+const char *jerk_status_str(jerk_status status);
+
+/* Fill *info.  Never fails on a valid plan. */
+jerk_status jerk_plan_info(jerk_plan plan, jerk_info *info);
+
+/* ---- single steps of the path (for parity checks and composition) ---- */
+
+/* Power normalisation only: for each block of norm_block bins (the last may
+ * be short), med = the element of rank floor((n-1)/2) of |F_k|^2 (FP64),
+ * F_k <- F_k (med / ln 2)^(-1/2); a block with med == 0 is copied.  The paper
+ * is silent on normalisation; this is the reading the library uses.
+ * d_in, d_out: complex64[n] device; may alias. */
+jerk_status jerk_normalise(jerk_plan plan, const void *d_in, int64_t n, void *d_out, void *stream);
+
+/* The FP64 taps of templates t0 .. t0+nt-1 (0 <= t0, t0+nt <= n_templates)
+ * into d_out: complex128 (interleaved double) [nt][K], tap d at index d + bM,
+ * zero outside the template's own half-width. */
+jerk_status jerk_taps(jerk_plan plan, int32_t t0, int32_t nt, void *d_out, void *stream);
+
+/* Power plane rows P[t][p] = |O_p(z_t, w_t)|^2 for templates t0 .. t0+nt-1
+ * and every cell p < b n, computed by the same fused overlap-and-save
+ * kernel as jerk_search, written to d_out: float32[nt][b n] (device).
+ * The spectrum is normalised first when norm_block > 0. */
+jerk_status jerk_plane(jerk_plan plan, const void *d_spec, int64_t n, int32_t t0, int32_t nt,
+                       float *d_out, void *stream);
+
+/* After a search: device pointer to the stage-`stage_idx` max-projection,
+ * uint64[n_cells] with n_cells = floor((b n - 1)/H) + 1, each entry
+ * (float bits of M_H(p)) << 32 | (0xFFFFFFFF - t).  Valid until the next
+ * search on the plan. */
+jerk_status jerk_maxproj(jerk_plan plan, int32_t stage_idx, const uint64_t **d_out, int64_t *n_cells);
+
+/* After a search (synchronises it): per stage mean and standard deviation
+ * of S_H over its defined cells (computed only in SIGMA mode, else 0) and
+ * the FP32 threshold applied.  Arrays of n_stages entries; any may be NULL. */
+jerk_status jerk_stats(jerk_plan plan, double *h_mean, double *h_std, float *h_theta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JERK_H_ */

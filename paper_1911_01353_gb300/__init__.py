@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) Fourier-domain jerk search.
+
+The search runs in the hand-written CUDA kernels of ``libjerk.so`` behind
+the C ABI in ``include/jerk.h``; ``jerk`` is its ctypes binding.
+"""
+from .jerk import (THRESH_ABS, THRESH_SIGMA, Candidate, Info, JerkError, Params, Plan, lib,  # noqa: F401
+                   make_params)

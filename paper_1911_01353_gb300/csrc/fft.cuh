@@ -1,0 +1,233 @@
+// Register/shared-memory FFT building blocks for the fused overlap-and-save
+// kernel (the paper's "shared memory implementation of the FFT", Sec. 2,
+// re-designed for sm_103a: 16 points per thread held in registers, radix-16
+// butterflies in registers, XOR-swizzled shared-memory transposes between
+// passes, no bank conflicts for any pass at L = 1024 .. 8192).
+//
+// Transform of length L = 2^LOG2L with NT = L/16 threads.  Each thread j
+// enters with x[j + NT m], m = 0..15, in registers and leaves with
+// y[rev(j) + NT r], r = 0..15, where y_v = sum_f x_f exp(SIGN 2 pi i f v / L)
+// (unnormalised; SIGN = +1 inverse, -1 forward) and rev(j) is the
+// mixed-radix digit reversal below.  Decimation in frequency, sub-problem-
+// major storage: after pass s the data are A_s[rho][f] at rho * N_s + f.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace jerk {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// XOR swizzle for 8-byte elements: conflict-free for every transpose used.
+__device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
+
+template <int LOG2L>
+struct FftCfg {
+    static constexpr int L = 1 << LOG2L;
+    static constexpr int NT = L / 16;
+    static constexpr int R0 = (LOG2L % 4) ? (1 << (LOG2L % 4)) : 16;   // radix of pass 0
+    static constexpr int I0 = 16 / R0;                                  // pass-0 items per thread
+    static constexpr int N0 = L / R0;                                   // sub-problem size after pass 0
+    static constexpr int NP = (LOG2L % 4) ? LOG2L / 4 : LOG2L / 4 - 1;  // radix-16 passes after pass 0
+    static_assert(LOG2L >= 10 && LOG2L <= 13, "L must be 1024..8192");
+};
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers, natural order in and out.
+// ---------------------------------------------------------------------------
+
+template <int SIGN>
+__device__ __forceinline__ float2 mul_i(float2 a) {  // (SIGN i) * a
+    return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
+    float2 s = cadd(a0, a1), d = csub(a0, a1);
+    a0 = s;
+    a1 = d;
+}
+
+template <int SIGN>
+__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+    float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    float2 s13 = cadd(a1, a3), d13 = mul_i<SIGN>(csub(a1, a3));
+    a0 = cadd(s02, s13);
+    a2 = csub(s02, s13);
+    a1 = cadd(d02, d13);
+    a3 = csub(d02, d13);
+}
+
+// exp(SIGN 2 pi i m / 16) as constants
+template <int SIGN, int M>
+__device__ __forceinline__ float2 w16() {
+    constexpr float c[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                             0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                             -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
+                             0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f};
+    constexpr float s[16] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                             1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                             0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
+                             -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f};
+    return make_float2(c[M % 16], SIGN > 0 ? s[M % 16] : -s[M % 16]);
+}
+
+// y_r = sum_k a_k exp(SIGN 2 pi i k r / 16): 4 x 4 split, k = k1 + 4 k2, r = r1 + 4 r2.
+template <int SIGN>
+__device__ __forceinline__ void dft16(float2 (&a)[16]) {
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(a[k1], a[k1 + 4], a[k1 + 8], a[k1 + 12]);
+    // a[k1 + 4 r1] = C[k1][r1]; twiddle by w16^(k1 r1)
+    a[5] = cmul(a[5], w16<SIGN, 1>());
+    a[9] = cmul(a[9], w16<SIGN, 2>());
+    a[13] = cmul(a[13], w16<SIGN, 3>());
+    a[6] = cmul(a[6], w16<SIGN, 2>());
+    a[10] = mul_i<SIGN>(a[10]);
+    a[14] = cmul(a[14], w16<SIGN, 6>());
+    a[7] = cmul(a[7], w16<SIGN, 3>());
+    a[11] = cmul(a[11], w16<SIGN, 6>());
+    a[15] = cmul(a[15], w16<SIGN, 9>());
+    // (k1 index is the fast one above; a[k1 + 4 r1] with r1 = element / 4)
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) dft4<SIGN>(a[4 * r1], a[4 * r1 + 1], a[4 * r1 + 2], a[4 * r1 + 3]);
+    // now a[r2 + 4 r1] = y[r1 + 4 r2]; transpose the 4x4 register block
+    float2 t;
+    t = a[1]; a[1] = a[4]; a[4] = t;
+    t = a[2]; a[2] = a[8]; a[8] = t;
+    t = a[3]; a[3] = a[12]; a[12] = t;
+    t = a[6]; a[6] = a[9]; a[9] = t;
+    t = a[7]; a[7] = a[13]; a[13] = t;
+    t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+// y_r = sum_k a_k exp(SIGN 2 pi i k r / 8): k = k1 + 2 k2, r = r1 + 4 r2.
+template <int SIGN>
+__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+    dft4<SIGN>(a[0], a[2], a[4], a[6]);   // k1 = 0 -> C[0][r1] at a[2 r1]
+    dft4<SIGN>(a[1], a[3], a[5], a[7]);   // k1 = 1 -> C[1][r1] at a[2 r1 + 1]
+    a[3] = cmul(a[3], w16<SIGN, 2>());    // w8^1
+    a[5] = mul_i<SIGN>(a[5]);             // w8^2
+    a[7] = cmul(a[7], w16<SIGN, 6>());    // w8^3
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) dft2<SIGN>(a[2 * r1], a[2 * r1 + 1]);
+    // a[r2 + 2 r1] = y[r1 + 4 r2] -> natural order
+    float2 y[8];
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) {
+        y[r1] = a[2 * r1];
+        y[r1 + 4] = a[2 * r1 + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = y[i];
+}
+
+template <int SIGN, int R>
+__device__ __forceinline__ void dft_small(float2 (&b)[R]) {
+    if constexpr (R == 2) {
+        dft2<SIGN>(b[0], b[1]);
+    } else if constexpr (R == 4) {
+        dft4<SIGN>(b[0], b[1], b[2], b[3]);
+    } else if constexpr (R == 8) {
+        dft8<SIGN>(b);
+    } else {
+        dft16<SIGN>(b);
+    }
+}
+
+// b[r] *= w^r for r = 1..R-1 (running product)
+template <int R>
+__device__ __forceinline__ void twiddle(float2 *b, float2 w) {
+    float2 acc = w;
+    b[1] = cmul(b[1], acc);
+#pragma unroll
+    for (int r = 2; r < R; ++r) {
+        acc = cmul(acc, w);
+        b[r] = cmul(b[r], acc);
+    }
+}
+
+// exp(SIGN 2 pi i num / den) for 0 <= num < den (den a power of two)
+template <int SIGN>
+__device__ __forceinline__ float2 unit_root(int num, int den) {
+    float s, c;
+    sincospif(2.0f * (float)num / (float)den, &s, &c);
+    return make_float2(c, SIGN > 0 ? s : -s);
+}
+
+// Per-thread twiddle bases, constant across transforms.
+template <int LOG2L, int SIGN>
+struct FftTw {
+    using C = FftCfg<LOG2L>;
+    float2 t0[C::I0];        // pass 0: w_L^{f1}, f1 = j + NT i
+    float2 ts[C::NP];        // pass s (1..NP-1): w_{N_{s-1}}^{f'}, f' = j mod N_s
+    __device__ __forceinline__ void init(int j) {
+#pragma unroll
+        for (int i = 0; i < C::I0; ++i) t0[i] = unit_root<SIGN>(j + C::NT * i, C::L);
+        int nprev = C::N0;
+#pragma unroll
+        for (int s = 1; s <= C::NP; ++s) {
+            const int ns = nprev / 16;
+            ts[s - 1] = unit_root<SIGN>(j & (ns - 1), nprev);
+            nprev = ns;
+        }
+    }
+};
+
+// digit reversal: thread j's outputs sit at rev(j) + NT r
+template <int LOG2L>
+__device__ __forceinline__ int fft_rev(int j) {
+    using C = FftCfg<LOG2L>;
+    int t = j, acc = 0;
+#pragma unroll
+    for (int i = 0; i < C::NP - 1; ++i) {
+        acc = acc * 16 + (t & 15);
+        t >>= 4;
+    }
+    return acc * C::R0 + t;
+}
+
+// The transform.  `work` is float2[L] shared memory; the call begins with a
+// barrier (so the previous transform's last reads are complete) and leaves
+// `work` free for reuse only after the caller's next barrier.
+template <int LOG2L, int SIGN>
+__device__ __forceinline__ void fft_run(float2 (&a)[16], float2 *__restrict__ work, int j,
+                                        const FftTw<LOG2L, SIGN> &tw) {
+    using C = FftCfg<LOG2L>;
+    constexpr int R0 = C::R0, I0 = C::I0, N0 = C::N0;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < I0; ++i) {
+        float2 b[R0];
+#pragma unroll
+        for (int k = 0; k < R0; ++k) b[k] = a[i + I0 * k];
+        dft_small<SIGN, R0>(b);
+        twiddle<R0>(b, tw.t0[i]);
+        const int f1 = j + C::NT * i;
+#pragma unroll
+        for (int r = 0; r < R0; ++r) work[swz(r * N0 + f1)] = b[r];
+    }
+    int nprev = N0;
+#pragma unroll
+    for (int s = 1; s <= C::NP; ++s) {
+        const int ns = nprev / 16;
+        const int rho = j / ns, fp = j & (ns - 1);
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[k] = work[swz(rho * nprev + fp + ns * k)];
+        dft16<SIGN>(a);
+        if (s < C::NP) {
+            twiddle<16>(a, tw.ts[s - 1]);
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 16; ++r) work[swz((rho * 16 + r) * ns + fp)] = a[r];
+        }
+        nprev = ns;
+    }
+}
+
+}  // namespace jerk

@@ -1,0 +1,133 @@
+// Internal declarations shared by the translation units of libjerk.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/jerk.h"
+
+namespace jerk {
+
+// Device-side candidate record written by the peak kernel.
+struct DevCand {
+    int64_t p;
+    int32_t t;
+    int32_t stage_idx;
+    float power;
+    int32_t pad;
+};
+
+// A fundamental template with its harmonic-row slots (h = 1 .. h_top).
+struct FundEntry {
+    int32_t t;
+    int32_t top_stage;       // index of the highest stage at which t is a valid fundamental
+    int64_t off[JERK_MAX_HARMONIC];   // slot offset (floats) of harmonic h = i + 1
+};
+
+// Arguments of the fused overlap-and-save kernel.
+struct ConvArgs {
+    const float2 *spec;      // normalised spectrum, N bins
+    int64_t N, bN;
+    const float2 *bank;      // [T][L] template spectra
+    int32_t T, tpg;          // templates, templates per group
+    int32_t V, bM;           // outputs kept per segment, overlap offset (b M)
+    int32_t nseg;
+    int32_t t0, nt;          // template range of this launch
+    // search mode
+    unsigned long long *M1;  // stage-1 max-projection, packed
+    const int32_t *slot_beg; // [T + 1] CSR into the slot entries
+    const int32_t *slot_h;
+    const int64_t *slot_off;
+    const int64_t *slot_len;
+    float *slots;
+    double *stat_part;       // [gridDim.y][gridDim.x][2]
+    // plane mode
+    float *plane;            // [nt][bN]
+};
+
+struct HarmArgs {
+    const float *slots;
+    const FundEntry *fund;
+    int32_t n_fund;
+    int32_t n_stages;
+    int32_t stages[JERK_MAX_STAGES];
+    int64_t n_cells[JERK_MAX_STAGES];     // floor((bN-1)/H) + 1
+    unsigned long long *M[JERK_MAX_STAGES];
+    double *stat_part;                     // [gridDim.x][n_stages][2]
+    int32_t f_chunk;                       // fundamentals per block (y split)
+};
+
+struct PeakArgs {
+    const unsigned long long *M[JERK_MAX_STAGES];
+    int64_t n_cells[JERK_MAX_STAGES];
+    const float *theta;                    // device, per stage
+    int32_t n_stages;
+    DevCand *out;
+    int64_t cap;
+    unsigned long long *count;
+};
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_normalise(const float2 *in, float2 *out, int64_t n, int block, cudaStream_t st);
+cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, int32_t t0, int32_t nt, int b, int pad,
+                        int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st);
+cudaError_t launch_template_fft(const double2 *taps, int32_t nt, int K, int L, const double2 *tw,
+                                float2 *bank, cudaStream_t st);
+cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st);
+cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int ngroups,
+                        cudaStream_t st);
+size_t conv_smem_bytes(int log2L);
+cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats,
+                            cudaStream_t st);
+cudaError_t launch_finalise_stats(const double *part1, int64_t n1, const double *partH, int64_t nH,
+                                  int n_stages, const double *counts, const float *thresh, int mode,
+                                  double *stats_out, float *theta_out, cudaStream_t st);
+cudaError_t launch_peaks(const PeakArgs &a, cudaStream_t st);
+
+// host helpers
+void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
+
+}  // namespace jerk
+
+struct jerk_plan_s {
+    jerk_params prm;
+    int device;
+    int b, nz, nw, T, M, K, L, log2L, V;
+    std::vector<int32_t> zt, wt, mt;   // grid values and per-template half-width
+    // device memory
+    float2 *d_bank = nullptr;
+    float2 *d_spec_in = nullptr;
+    float2 *d_spec_norm = nullptr;
+    unsigned long long *d_M[JERK_MAX_STAGES] = {nullptr, nullptr, nullptr, nullptr};
+    float *d_slots = nullptr;
+    int64_t slot_cap = 0;              // floats
+    int32_t *d_zt = nullptr, *d_wt = nullptr;
+    int32_t *d_slot_beg = nullptr, *d_slot_h = nullptr;
+    int64_t *d_slot_off = nullptr, *d_slot_len = nullptr;
+    jerk::FundEntry *d_fund = nullptr;
+    int n_entries = 0, n_fund = 0;
+    double *d_stat_part = nullptr;     // conv partials then harmonic partials
+    int64_t stat_part_cap = 0;         // doubles
+    double *d_stats = nullptr;         // [n_stages][2]
+    double *d_counts = nullptr;        // [n_stages]
+    float *d_thresh = nullptr;         // [n_stages] user thresholds
+    float *d_theta = nullptr;          // [n_stages] applied thresholds
+    jerk::DevCand *d_cand = nullptr;
+    unsigned long long *d_count = nullptr;
+    double2 *d_gl = nullptr;
+    int n_gl = 0;
+    int64_t bytes = 0;
+    // host-side slot tables for the current n
+    std::vector<int32_t> h_slot_beg, h_slot_h;
+    std::vector<int64_t> h_slot_off, h_slot_len;
+    std::vector<jerk::FundEntry> h_fund;
+    int64_t tables_n = -1;
+    // state
+    bool templates_ready = false;
+    int64_t last_n = 0;
+    bool searched = false;
+    cudaEvent_t done = nullptr;
+    jerk::DevCand *h_cand = nullptr;   // pinned staging for candidates
+};

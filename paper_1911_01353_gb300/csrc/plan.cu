@@ -1,0 +1,613 @@
+// Host side of libjerk.so: parameter validation, plan sizing, the template
+// bank, the launch sequence of a search and the candidate read-back.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "jerk_internal.h"
+
+using namespace jerk;
+
+namespace {
+
+constexpr int kSMs = 152;
+constexpr size_t kGroupBytes = 32u << 20;   // bank slice a template group keeps in L2
+
+jerk_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return JERK_OK;
+    if (e == cudaErrorMemoryAllocation) return JERK_ENOMEM;
+    return JERK_ECUDA;
+}
+
+#define JCHECK(x)                                  \
+    do {                                           \
+        cudaError_t e_ = (x);                      \
+        if (e_ != cudaSuccess) return from_cuda(e_); \
+    } while (0)
+
+int halfwidth(int z, int w, int pad) { return (4 * std::abs(z) + std::abs(w) + 7) / 8 + pad; }
+
+int64_t n_cells(int64_t bN, int H) { return (bN - 1) / H + 1; }
+
+// passes of the transform (pass 0 + radix-16 passes) as a cost proxy
+int fft_passes(int log2L) { return (log2L % 4) ? log2L / 4 + 1 : log2L / 4; }
+
+bool valid_at(const jerk_plan_s *pl, int t, int H) {
+    return (int64_t)H * std::abs(pl->zt[t]) <= pl->prm.zmax && (int64_t)H * std::abs(pl->wt[t]) <= pl->prm.wmax;
+}
+
+int index_of(const jerk_plan_s *pl, int z, int w) {
+    const int i = (z + pl->prm.zmax) / pl->prm.dz;
+    const int j = (w + pl->prm.wmax) / pl->prm.dw;
+    return j * pl->nz + i;
+}
+
+// Slot tables for spectra of n bins: for every harmonic h of every
+// fundamental valid at the smallest stage >= max(h, 2), one float row of
+// n_cells(bN, that stage) entries indexed by the fundamental cell p.
+int64_t build_tables(jerk_plan_s *pl, int64_t n, bool fill) {
+    const int64_t bN = (int64_t)pl->b * n;
+    const int ns = pl->prm.n_stages;
+    struct Ent { int32_t t, h; int64_t off, len; };
+    std::vector<Ent> ents;
+    std::vector<FundEntry> fund;
+    int64_t off = 0;
+    if (ns > 1) {
+        for (int t = 0; t < pl->T; ++t) {
+            int top = 0;
+            for (int si = 1; si < ns; ++si)
+                if (valid_at(pl, t, pl->prm.stages[si])) top = si;
+            if (top == 0) continue;
+            FundEntry fe;
+            std::memset(&fe, 0, sizeof(fe));
+            fe.t = t;
+            fe.top_stage = top;
+            const int Htop = pl->prm.stages[top];
+            for (int h = 1; h <= Htop; ++h) {
+                int sn = 1;
+                while (pl->prm.stages[sn] < std::max(h, 2)) ++sn;
+                const int64_t len = n_cells(bN, pl->prm.stages[sn]);
+                fe.off[h - 1] = off;
+                if (fill) ents.push_back({index_of(pl, h * pl->zt[t], h * pl->wt[t]), h, off, len});
+                off += len;
+            }
+            if (fill) fund.push_back(fe);
+        }
+    }
+    if (fill) {
+        std::stable_sort(ents.begin(), ents.end(), [](const Ent &x, const Ent &y) { return x.t < y.t; });
+        pl->h_slot_beg.assign(pl->T + 1, 0);
+        pl->h_slot_h.resize(ents.size());
+        pl->h_slot_off.resize(ents.size());
+        pl->h_slot_len.resize(ents.size());
+        for (size_t e = 0; e < ents.size(); ++e) {
+            pl->h_slot_beg[ents[e].t + 1]++;
+            pl->h_slot_h[e] = ents[e].h;
+            pl->h_slot_off[e] = ents[e].off;
+            pl->h_slot_len[e] = ents[e].len;
+        }
+        for (int t = 0; t < pl->T; ++t) pl->h_slot_beg[t + 1] += pl->h_slot_beg[t];
+        pl->h_fund = fund;
+        pl->n_entries = (int)ents.size();
+        pl->n_fund = (int)fund.size();
+    }
+    return off;
+}
+
+int nseg_for(const jerk_plan_s *pl, int64_t n) {
+    const int64_t bN = (int64_t)pl->b * n;
+    return (int)((bN + pl->V - 1) / pl->V);
+}
+
+int tpg_for(const jerk_plan_s *pl, int nseg, int nt) {
+    const int64_t target = (int64_t)kSMs * 6;
+    int64_t tpg = ((int64_t)nt * nseg + target - 1) / target;
+    const int64_t cap = std::max<int64_t>(1, (int64_t)(kGroupBytes / ((size_t)pl->L * sizeof(float2))));
+    tpg = std::min<int64_t>(std::max<int64_t>(tpg, 8), cap);
+    tpg = std::min<int64_t>(tpg, nt);
+    return (int)std::max<int64_t>(tpg, 1);
+}
+
+jerk_status validate(const jerk_params *p) {
+    if (!p) return JERK_EINVAL;
+    if (p->dz <= 0 || p->dw <= 0 || p->zmax < 0 || p->wmax < 0) return JERK_EINVAL;
+    if (p->zmax % p->dz || p->wmax % p->dw) return JERK_EINVAL;
+    if (p->zmax > 4096 || p->wmax > 32768) return JERK_EINVAL;
+    if (p->numbetween != 2) return JERK_EINVAL;
+    if (p->pad_bins < 1 || p->pad_bins > 1024) return JERK_EINVAL;
+    if (p->n_stages < 1 || p->n_stages > JERK_MAX_STAGES) return JERK_EINVAL;
+    if (p->stages[0] != 1) return JERK_EINVAL;
+    for (int i = 1; i < p->n_stages; ++i)
+        if (p->stages[i] <= p->stages[i - 1] || p->stages[i] > JERK_MAX_HARMONIC) return JERK_EINVAL;
+    if (p->thresh_mode != JERK_THRESH_ABS && p->thresh_mode != JERK_THRESH_SIGMA) return JERK_EINVAL;
+    for (int i = 0; i < p->n_stages; ++i)
+        if (!std::isfinite(p->thresh[i])) return JERK_EINVAL;
+    if (p->norm_block < 0 || p->norm_block > 4096) return JERK_EINVAL;
+    if (p->precision != 0) return JERK_EINVAL;
+    if (p->max_bins < 1 || p->max_bins > ((int64_t)1 << 30)) return JERK_EINVAL;
+    if (p->max_candidates < 1 || p->max_candidates > ((int64_t)1 << 26)) return JERK_EINVAL;
+    if (p->seg_len != 0 && (p->seg_len < 1024 || p->seg_len > 8192 || (p->seg_len & (p->seg_len - 1))))
+        return JERK_EINVAL;
+    return JERK_OK;
+}
+
+template <typename T>
+cudaError_t dalloc(jerk_plan_s *pl, T **ptr, size_t count) {
+    *ptr = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
+    if (e == cudaSuccess) pl->bytes += (int64_t)(count * sizeof(T));
+    return e;
+}
+
+void release(jerk_plan_s *pl) {
+    cudaFree(pl->d_bank);
+    cudaFree(pl->d_spec_in);
+    cudaFree(pl->d_spec_norm);
+    for (auto &m : pl->d_M) cudaFree(m);
+    cudaFree(pl->d_slots);
+    cudaFree(pl->d_zt);
+    cudaFree(pl->d_wt);
+    cudaFree(pl->d_slot_beg);
+    cudaFree(pl->d_slot_h);
+    cudaFree(pl->d_slot_off);
+    cudaFree(pl->d_slot_len);
+    cudaFree(pl->d_fund);
+    cudaFree(pl->d_stat_part);
+    cudaFree(pl->d_stats);
+    cudaFree(pl->d_counts);
+    cudaFree(pl->d_thresh);
+    cudaFree(pl->d_theta);
+    cudaFree(pl->d_cand);
+    cudaFree(pl->d_count);
+    cudaFree(pl->d_gl);
+    if (pl->h_cand) cudaFreeHost(pl->h_cand);
+    if (pl->done) cudaEventDestroy(pl->done);
+}
+
+// upload the slot tables for spectra of n bins (synchronous w.r.t. the host buffers)
+jerk_status ensure_tables(jerk_plan_s *pl, int64_t n, cudaStream_t st) {
+    if (pl->tables_n == n) return JERK_OK;
+    const int64_t need = build_tables(pl, n, true);
+    if (need > pl->slot_cap) return JERK_ENOMEM;
+    JCHECK(cudaMemcpyAsync(pl->d_slot_beg, pl->h_slot_beg.data(), sizeof(int32_t) * (pl->T + 1),
+                           cudaMemcpyHostToDevice, st));
+    if (pl->n_entries) {
+        JCHECK(cudaMemcpyAsync(pl->d_slot_h, pl->h_slot_h.data(), sizeof(int32_t) * pl->n_entries,
+                               cudaMemcpyHostToDevice, st));
+        JCHECK(cudaMemcpyAsync(pl->d_slot_off, pl->h_slot_off.data(), sizeof(int64_t) * pl->n_entries,
+                               cudaMemcpyHostToDevice, st));
+        JCHECK(cudaMemcpyAsync(pl->d_slot_len, pl->h_slot_len.data(), sizeof(int64_t) * pl->n_entries,
+                               cudaMemcpyHostToDevice, st));
+    }
+    if (pl->n_fund)
+        JCHECK(cudaMemcpyAsync(pl->d_fund, pl->h_fund.data(), sizeof(FundEntry) * pl->n_fund,
+                               cudaMemcpyHostToDevice, st));
+    // host vectors are reused by later calls: make sure the copies have been consumed
+    JCHECK(cudaStreamSynchronize(st));
+    pl->tables_n = n;
+    return JERK_OK;
+}
+
+const float2 *normalised_input(jerk_plan_s *pl, const void *d_spec, int64_t n, cudaStream_t st, cudaError_t *err) {
+    *err = cudaSuccess;
+    if (pl->prm.norm_block > 0) {
+        *err = launch_normalise((const float2 *)d_spec, pl->d_spec_norm, n, pl->prm.norm_block, st);
+        return pl->d_spec_norm;
+    }
+    return (const float2 *)d_spec;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *jerk_status_str(jerk_status s) {
+    switch (s) {
+        case JERK_OK: return "JERK_OK";
+        case JERK_EINVAL: return "JERK_EINVAL: invalid argument";
+        case JERK_ENOMEM: return "JERK_ENOMEM: out of memory";
+        case JERK_ECUDA: return "JERK_ECUDA: CUDA error";
+        case JERK_ETIMEOUT: return "JERK_ETIMEOUT: device wait expired";
+        case JERK_EOVERFLOW: return "JERK_EOVERFLOW: candidate buffer too small";
+        case JERK_ESTATE: return "JERK_ESTATE: call out of order";
+    }
+    return "unknown jerk_status";
+}
+
+jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *out) {
+    if (!out) return JERK_EINVAL;
+    *out = nullptr;
+    jerk_status v = validate(params);
+    if (v != JERK_OK) return v;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(device));
+
+    jerk_plan_s *pl = new (std::nothrow) jerk_plan_s();
+    if (!pl) return JERK_ENOMEM;
+    pl->prm = *params;
+    pl->device = device;
+    pl->b = params->numbetween;
+    pl->nz = 2 * params->zmax / params->dz + 1;
+    pl->nw = 2 * params->wmax / params->dw + 1;
+    pl->T = pl->nz * pl->nw;
+    pl->zt.resize(pl->T);
+    pl->wt.resize(pl->T);
+    pl->mt.resize(pl->T);
+    pl->M = 0;
+    for (int j = 0; j < pl->nw; ++j)
+        for (int i = 0; i < pl->nz; ++i) {
+            const int t = j * pl->nz + i;
+            pl->zt[t] = -params->zmax + i * params->dz;
+            pl->wt[t] = -params->wmax + j * params->dw;
+            pl->mt[t] = halfwidth(pl->zt[t], pl->wt[t], params->pad_bins);
+            pl->M = std::max(pl->M, pl->mt[t]);
+        }
+    pl->K = 2 * pl->b * pl->M + 1;
+    if (params->seg_len) {
+        pl->L = params->seg_len;
+    } else {
+        double best = 1e300;
+        for (int lg = 10; lg <= 13; ++lg) {
+            const int L = 1 << lg, V = L - pl->K + 1;
+            if (V < L / 4) continue;
+            const double cost = (fft_passes(lg) + 1.0) * L / V;
+            if (cost < best - 1e-9) {
+                best = cost;
+                pl->L = L;
+            }
+        }
+        if (best >= 1e300) {
+            delete pl;
+            return JERK_EINVAL;
+        }
+    }
+    pl->log2L = 0;
+    while ((1 << pl->log2L) < pl->L) ++pl->log2L;
+    pl->V = pl->L - pl->K + 1;
+    if (pl->V < 64) {
+        delete pl;
+        return JERK_EINVAL;
+    }
+
+    const int64_t N = params->max_bins, bN = (int64_t)pl->b * N;
+    const int ns = params->n_stages;
+    pl->slot_cap = build_tables(pl, N, false);
+    // largest conv grid over every spectrum length the plan accepts
+    int64_t conv_blocks = 0;
+    for (int nseg = 1; nseg <= nseg_for(pl, N); ++nseg) {
+        const int tpg = tpg_for(pl, nseg, pl->T);
+        conv_blocks = std::max<int64_t>(conv_blocks, (int64_t)nseg * ((pl->T + tpg - 1) / tpg));
+    }
+    const int64_t harm_blocks = ns > 1 ? (n_cells(bN, params->stages[1]) + 255) / 256 : 0;
+    pl->stat_part_cap = 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
+
+    // does it fit?
+    size_t free_b = 0, total_b = 0;
+    JCHECK(cudaMemGetInfo(&free_b, &total_b));
+    int64_t need = (int64_t)pl->T * pl->L * 8 + 2 * N * 8 + pl->slot_cap * 4 + pl->stat_part_cap * 8 +
+                   params->max_candidates * (int64_t)sizeof(DevCand) + (int64_t)pl->T * 40;
+    for (int si = 0; si < ns; ++si) need += n_cells(bN, params->stages[si]) * 8;
+    if ((double)need > 0.97 * (double)free_b) {
+        delete pl;
+        return JERK_ENOMEM;
+    }
+
+    cudaError_t e = cudaSuccess;
+#define TRY(x) \
+    if (e == cudaSuccess) e = (x)
+    TRY(dalloc(pl, &pl->d_bank, (size_t)pl->T * pl->L));
+    TRY(dalloc(pl, &pl->d_spec_in, (size_t)N));
+    TRY(dalloc(pl, &pl->d_spec_norm, (size_t)N));
+    for (int si = 0; si < ns; ++si) TRY(dalloc(pl, &pl->d_M[si], (size_t)n_cells(bN, params->stages[si])));
+    TRY(dalloc(pl, &pl->d_slots, (size_t)pl->slot_cap));
+    TRY(dalloc(pl, &pl->d_zt, (size_t)pl->T));
+    TRY(dalloc(pl, &pl->d_wt, (size_t)pl->T));
+    TRY(dalloc(pl, &pl->d_slot_beg, (size_t)pl->T + 1));
+    // entry / fundamental counts do not depend on n
+    build_tables(pl, N, true);
+    pl->tables_n = -1;
+    TRY(dalloc(pl, &pl->d_slot_h, (size_t)pl->n_entries));
+    TRY(dalloc(pl, &pl->d_slot_off, (size_t)pl->n_entries));
+    TRY(dalloc(pl, &pl->d_slot_len, (size_t)pl->n_entries));
+    TRY(dalloc(pl, &pl->d_fund, (size_t)pl->n_fund));
+    TRY(dalloc(pl, &pl->d_stat_part, (size_t)pl->stat_part_cap));
+    TRY(dalloc(pl, &pl->d_stats, (size_t)2 * JERK_MAX_STAGES));
+    TRY(dalloc(pl, &pl->d_counts, (size_t)JERK_MAX_STAGES));
+    TRY(dalloc(pl, &pl->d_thresh, (size_t)JERK_MAX_STAGES));
+    TRY(dalloc(pl, &pl->d_theta, (size_t)JERK_MAX_STAGES));
+    TRY(dalloc(pl, &pl->d_cand, (size_t)params->max_candidates));
+    TRY(dalloc(pl, &pl->d_count, 1));
+    TRY(dalloc(pl, &pl->d_gl, 64));
+    TRY(cudaMallocHost((void **)&pl->h_cand, sizeof(DevCand) * (size_t)params->max_candidates));
+    TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    TRY(cudaMemcpy(pl->d_zt, pl->zt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(pl->d_wt, pl->wt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(pl->d_thresh, params->thresh, sizeof(float) * JERK_MAX_STAGES, cudaMemcpyHostToDevice));
+    if (e == cudaSuccess) {
+        std::vector<double> x, w;
+        gauss_legendre(64, x, w);
+        std::vector<double2> gl(64);
+        for (int i = 0; i < 64; ++i) gl[i] = make_double2(x[i], w[i]);
+        e = cudaMemcpy(pl->d_gl, gl.data(), sizeof(double2) * 64, cudaMemcpyHostToDevice);
+        pl->n_gl = 64;
+    }
+#undef TRY
+    if (e != cudaSuccess) {
+        release(pl);
+        delete pl;
+        return from_cuda(e);
+    }
+    *out = pl;
+    return JERK_OK;
+}
+
+jerk_status jerk_plan_destroy(jerk_plan pl) {
+    if (!pl) return JERK_OK;
+    cudaSetDevice(pl->device);
+    if (pl->done) cudaEventSynchronize(pl->done);
+    release(pl);
+    delete pl;
+    return JERK_OK;
+}
+
+jerk_status jerk_plan_info(jerk_plan pl, jerk_info *info) {
+    if (!pl || !info) return JERK_EINVAL;
+    info->nz = pl->nz;
+    info->nw = pl->nw;
+    info->n_templates = pl->T;
+    info->bank_halfwidth = pl->M;
+    info->taps = pl->K;
+    info->seg_len = pl->L;
+    info->seg_valid = pl->V;
+    info->device = pl->device;
+    info->max_bins = pl->prm.max_bins;
+    info->slot_floats = pl->slot_cap;
+    info->workspace_bytes = pl->bytes;
+    info->d_bank = pl->d_bank;
+    return JERK_OK;
+}
+
+jerk_status jerk_taps(jerk_plan pl, int32_t t0, int32_t nt, void *d_out, void *stream) {
+    if (!pl || !d_out || t0 < 0 || nt < 1 || (int64_t)t0 + nt > pl->T) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(launch_taps(pl->d_zt, pl->d_wt, t0, nt, pl->b, pl->prm.pad_bins, pl->b * pl->M, pl->d_gl, pl->n_gl,
+                       (double2 *)d_out, st));
+    return JERK_OK;
+}
+
+jerk_status jerk_templates(jerk_plan pl, void *stream) {
+    if (!pl) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    // process the bank in chunks so the FP64 tap buffer stays small
+    const int chunk = std::max(1, std::min(pl->T, (int)((256u << 20) / ((size_t)pl->K * sizeof(double2)))));
+    double2 *taps = nullptr, *tw = nullptr;
+    JCHECK(cudaMallocAsync((void **)&taps, (size_t)chunk * pl->K * sizeof(double2), st));
+    cudaError_t e = cudaMallocAsync((void **)&tw, (size_t)(pl->L / 2) * sizeof(double2), st);
+    if (e == cudaSuccess) e = launch_twiddles64(tw, pl->L, st);
+    for (int t0 = 0; t0 < pl->T && e == cudaSuccess; t0 += chunk) {
+        const int nt = std::min(chunk, pl->T - t0);
+        e = launch_taps(pl->d_zt, pl->d_wt, t0, nt, pl->b, pl->prm.pad_bins, pl->b * pl->M, pl->d_gl, pl->n_gl,
+                        taps, st);
+        if (e == cudaSuccess) e = launch_template_fft(taps, nt, pl->K, pl->L, tw, pl->d_bank + (size_t)t0 * pl->L, st);
+    }
+    cudaFreeAsync(taps, st);
+    if (tw) cudaFreeAsync(tw, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    JCHECK(cudaEventRecord(pl->done, st));
+    pl->templates_ready = true;
+    return JERK_OK;
+}
+
+jerk_status jerk_normalise(jerk_plan pl, const void *d_in, int64_t n, void *d_out, void *stream) {
+    if (!pl || !d_in || !d_out || n < 1) return JERK_EINVAL;
+    if (pl->prm.norm_block < 1) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(pl->device));
+    JCHECK(launch_normalise((const float2 *)d_in, (float2 *)d_out, n, pl->prm.norm_block, (cudaStream_t)stream));
+    return JERK_OK;
+}
+
+jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, int32_t nt, float *d_out,
+                       void *stream) {
+    if (!pl || !d_spec || !d_out || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
+    if (t0 < 0 || nt < 1 || (int64_t)t0 + nt > pl->T) return JERK_EINVAL;
+    if (!pl->templates_ready) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    cudaError_t e;
+    const float2 *spec = normalised_input(pl, d_spec, n, st, &e);
+    JCHECK(e);
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.spec = spec;
+    a.N = n;
+    a.bN = (int64_t)pl->b * n;
+    a.bank = pl->d_bank;
+    a.T = pl->T;
+    a.V = pl->V;
+    a.bM = pl->b * pl->M;
+    a.nseg = nseg_for(pl, n);
+    a.tpg = tpg_for(pl, a.nseg, nt);
+    a.t0 = t0;
+    a.nt = nt;
+    a.plane = d_out;
+    const int ngroups = (nt + a.tpg - 1) / a.tpg;
+    JCHECK(launch_conv(pl->log2L, 1, false, a, ngroups, st));
+    JCHECK(cudaEventRecord(pl->done, st));
+    return JERK_OK;
+}
+
+jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *stream) {
+    if (!pl || !d_spec || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
+    if (!pl->templates_ready) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    jerk_status s = ensure_tables(pl, n, st);
+    if (s != JERK_OK) return s;
+    const int ns = pl->prm.n_stages;
+    const int64_t bN = (int64_t)pl->b * n;
+    const bool sigma = pl->prm.thresh_mode == JERK_THRESH_SIGMA;
+
+    cudaError_t e;
+    const float2 *spec = normalised_input(pl, d_spec, n, st, &e);
+    JCHECK(e);
+    for (int si = 0; si < ns; ++si)
+        JCHECK(cudaMemsetAsync(pl->d_M[si], 0, sizeof(unsigned long long) * n_cells(bN, pl->prm.stages[si]), st));
+
+    // fused overlap-and-save + stage-1 max-projection + harmonic rows
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.spec = spec;
+    a.N = n;
+    a.bN = bN;
+    a.bank = pl->d_bank;
+    a.T = pl->T;
+    a.V = pl->V;
+    a.bM = pl->b * pl->M;
+    a.nseg = nseg_for(pl, n);
+    a.tpg = tpg_for(pl, a.nseg, pl->T);
+    a.t0 = 0;
+    a.nt = pl->T;
+    a.M1 = pl->d_M[0];
+    a.slot_beg = pl->d_slot_beg;
+    a.slot_h = pl->d_slot_h;
+    a.slot_off = pl->d_slot_off;
+    a.slot_len = pl->d_slot_len;
+    a.slots = pl->d_slots;
+    a.stat_part = pl->d_stat_part;
+    const int ngroups = (pl->T + a.tpg - 1) / a.tpg;
+    const int64_t n1 = (int64_t)a.nseg * ngroups;
+    JCHECK(launch_conv(pl->log2L, 0, sigma, a, ngroups, st));
+
+    // harmonic sums for stages > 1
+    int64_t nH = 0;
+    double *partH = pl->d_stat_part + 2 * n1;
+    double counts[JERK_MAX_STAGES] = {0, 0, 0, 0};
+    counts[0] = (double)bN * pl->T;
+    if (ns > 1) {
+        HarmArgs h;
+        std::memset(&h, 0, sizeof(h));
+        h.slots = pl->d_slots;
+        h.fund = pl->d_fund;
+        h.n_fund = pl->n_fund;
+        h.n_stages = ns;
+        for (int si = 0; si < ns; ++si) {
+            h.stages[si] = pl->prm.stages[si];
+            h.n_cells[si] = n_cells(bN, pl->prm.stages[si]);
+            h.M[si] = pl->d_M[si];
+        }
+        h.stat_part = partH;
+        h.f_chunk = pl->n_fund;
+        const int64_t nthreads = h.n_cells[1];
+        nH = (nthreads + 255) / 256;
+        JCHECK(launch_harmonic(h, nthreads, 1, sigma, st));
+        for (int si = 1; si < ns; ++si) {
+            int64_t nf = 0;
+            for (const auto &fe : pl->h_fund)
+                if (fe.top_stage >= si) ++nf;
+            counts[si] = (double)nf * h.n_cells[si];
+        }
+    }
+    JCHECK(cudaMemcpyAsync(pl->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, st));
+    JCHECK(launch_finalise_stats(pl->d_stat_part, n1, partH, nH, ns, pl->d_counts, pl->d_thresh,
+                                 pl->prm.thresh_mode, pl->d_stats, pl->d_theta, st));
+
+    // peaks
+    JCHECK(cudaMemsetAsync(pl->d_count, 0, sizeof(unsigned long long), st));
+    PeakArgs pk;
+    std::memset(&pk, 0, sizeof(pk));
+    for (int si = 0; si < ns; ++si) {
+        pk.M[si] = pl->d_M[si];
+        pk.n_cells[si] = n_cells(bN, pl->prm.stages[si]);
+    }
+    pk.theta = pl->d_theta;
+    pk.n_stages = ns;
+    pk.out = pl->d_cand;
+    pk.cap = pl->prm.max_candidates;
+    pk.count = pl->d_count;
+    JCHECK(launch_peaks(pk, st));
+    JCHECK(cudaEventRecord(pl->done, st));
+    pl->last_n = n;
+    pl->searched = true;
+    return JERK_OK;
+}
+
+jerk_status jerk_search_host(jerk_plan pl, const void *h_spec, int64_t n, void *stream) {
+    if (!pl || !h_spec || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
+    if (!pl->templates_ready) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    JCHECK(cudaMemcpyAsync(pl->d_spec_in, h_spec, (size_t)n * sizeof(float2), cudaMemcpyHostToDevice, st));
+    return jerk_search(pl, pl->d_spec_in, n, stream);
+}
+
+jerk_status jerk_candidates(jerk_plan pl, jerk_candidate *h_out, int64_t cap, int64_t *n_out) {
+    if (!pl || !n_out || cap < 0 || (cap > 0 && !h_out)) return JERK_EINVAL;
+    if (!pl->searched) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    JCHECK(cudaEventSynchronize(pl->done));
+    unsigned long long cnt = 0;
+    JCHECK(cudaMemcpy(&cnt, pl->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
+    const int64_t kept = std::min<int64_t>((int64_t)cnt, pl->prm.max_candidates);
+    if (kept > 0)
+        JCHECK(cudaMemcpy(pl->h_cand, pl->d_cand, sizeof(DevCand) * (size_t)kept, cudaMemcpyDeviceToHost));
+    std::vector<DevCand> v(pl->h_cand, pl->h_cand + kept);
+    std::sort(v.begin(), v.end(), [](const DevCand &x, const DevCand &y) {
+        return x.stage_idx != y.stage_idx ? x.stage_idx < y.stage_idx : x.p < y.p;
+    });
+    const int64_t ncopy = std::min<int64_t>(kept, cap);
+    for (int64_t i = 0; i < ncopy; ++i) {
+        jerk_candidate &c = h_out[i];
+        const DevCand &d = v[i];
+        const int t = d.t;
+        c.p = d.p;
+        c.r = (double)d.p / pl->b;
+        c.t = t;
+        c.z_idx = (t >= 0 && t < pl->T) ? t % pl->nz : -1;
+        c.w_idx = (t >= 0 && t < pl->T) ? t / pl->nz : -1;
+        c.stage = pl->prm.stages[d.stage_idx];
+        c.z = (t >= 0 && t < pl->T) ? (float)pl->zt[t] : 0.f;
+        c.w = (t >= 0 && t < pl->T) ? (float)pl->wt[t] : 0.f;
+        c.power = d.power;
+        c.reserved = 0;
+    }
+    *n_out = (int64_t)cnt;
+    if ((int64_t)cnt > pl->prm.max_candidates || (int64_t)cnt > cap) return JERK_EOVERFLOW;
+    return JERK_OK;
+}
+
+jerk_status jerk_maxproj(jerk_plan pl, int32_t stage_idx, const uint64_t **d_out, int64_t *n_cells_out) {
+    if (!pl || !d_out || !n_cells_out || stage_idx < 0 || stage_idx >= pl->prm.n_stages) return JERK_EINVAL;
+    if (!pl->searched) return JERK_ESTATE;
+    *d_out = (const uint64_t *)pl->d_M[stage_idx];
+    *n_cells_out = n_cells((int64_t)pl->b * pl->last_n, pl->prm.stages[stage_idx]);
+    return JERK_OK;
+}
+
+jerk_status jerk_stats(jerk_plan pl, double *h_mean, double *h_std, float *h_theta) {
+    if (!pl) return JERK_EINVAL;
+    if (!pl->searched) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    JCHECK(cudaEventSynchronize(pl->done));
+    double st[2 * JERK_MAX_STAGES];
+    float th[JERK_MAX_STAGES];
+    JCHECK(cudaMemcpy(st, pl->d_stats, sizeof(st), cudaMemcpyDeviceToHost));
+    JCHECK(cudaMemcpy(th, pl->d_theta, sizeof(th), cudaMemcpyDeviceToHost));
+    for (int si = 0; si < pl->prm.n_stages; ++si) {
+        if (h_mean) h_mean[si] = st[2 * si];
+        if (h_std) h_std[si] = st[2 * si + 1];
+        if (h_theta) h_theta[si] = th[si];
+    }
+    return JERK_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,236 @@
+"""ctypes binding of libjerk.so (argument marshalling only).
+
+Every step of the search runs in the library's CUDA kernels; this module only
+converts Python/PyTorch arguments into the C ABI declared in
+``include/jerk.h``.  PyTorch supplies device memory and streams.  If the
+library is missing the import of ``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libjerk.so")
+
+JERK_OK, JERK_EINVAL, JERK_ENOMEM, JERK_ECUDA, JERK_ETIMEOUT, JERK_EOVERFLOW, JERK_ESTATE = range(7)
+THRESH_ABS, THRESH_SIGMA = 0, 1
+
+# Every function the header declares (kept in step with include/jerk.h).
+EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host",
+           "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
+           "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("zmax", ctypes.c_int32), ("dz", ctypes.c_int32),
+                ("wmax", ctypes.c_int32), ("dw", ctypes.c_int32),
+                ("numbetween", ctypes.c_int32), ("pad_bins", ctypes.c_int32),
+                ("seg_len", ctypes.c_int32), ("n_stages", ctypes.c_int32),
+                ("stages", ctypes.c_int32 * 4), ("thresh_mode", ctypes.c_int32),
+                ("thresh", ctypes.c_float * 4), ("norm_block", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_bins", ctypes.c_int64),
+                ("max_candidates", ctypes.c_int64)]
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int64), ("r", ctypes.c_double), ("t", ctypes.c_int32),
+                ("z_idx", ctypes.c_int32), ("w_idx", ctypes.c_int32), ("stage", ctypes.c_int32),
+                ("z", ctypes.c_float), ("w", ctypes.c_float), ("power", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nz", ctypes.c_int32), ("nw", ctypes.c_int32), ("n_templates", ctypes.c_int32),
+                ("bank_halfwidth", ctypes.c_int32), ("taps", ctypes.c_int32),
+                ("seg_len", ctypes.c_int32), ("seg_valid", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("max_bins", ctypes.c_int64), ("slot_floats", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64), ("d_bank", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libjerk.so (built by ``paper_1911_01353_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libjerk.so is not built (%s); run "
+                               "`python -m paper_1911_01353_gb300.build`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        st = ctypes.c_int
+        sig = {
+            "jerk_plan_create": ([ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(vp)], st),
+            "jerk_templates": ([vp, vp], st),
+            "jerk_search": ([vp, vp, i64, vp], st),
+            "jerk_search_host": ([vp, vp, i64, vp], st),
+            "jerk_candidates": ([vp, ctypes.POINTER(Candidate), i64, ctypes.POINTER(i64)], st),
+            "jerk_plan_destroy": ([vp], st),
+            "jerk_status_str": ([st], ctypes.c_char_p),
+            "jerk_plan_info": ([vp, ctypes.POINTER(Info)], st),
+            "jerk_normalise": ([vp, vp, i64, vp, vp], st),
+            "jerk_taps": ([vp, i32, i32, vp, vp], st),
+            "jerk_plane": ([vp, vp, i64, i32, i32, vp, vp], st),
+            "jerk_maxproj": ([vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i64)], st),
+            "jerk_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_float)], st),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+class JerkError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__("%s: %s" % (what, lib().jerk_status_str(code).decode()))
+
+
+def _check(code: int, what: str):
+    if code != JERK_OK:
+        raise JerkError(code, what)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def make_params(zmax, dz, wmax, dw, stages=(1, 2), thresh=(15.0, 20.0), thresh_mode=THRESH_ABS,
+                pad_bins=16, seg_len=0, norm_block=1024, max_bins=1 << 16, max_candidates=1 << 16,
+                numbetween=2, precision=0) -> Params:
+    p = Params()
+    p.zmax, p.dz, p.wmax, p.dw = zmax, dz, wmax, dw
+    p.numbetween, p.pad_bins, p.seg_len = numbetween, pad_bins, seg_len
+    p.n_stages = len(stages)
+    for i in range(4):
+        p.stages[i] = stages[i] if i < len(stages) else 0
+        p.thresh[i] = thresh[i] if i < len(thresh) else 0.0
+    p.thresh_mode = thresh_mode
+    p.norm_block, p.precision = norm_block, precision
+    p.max_bins, p.max_candidates = max_bins, max_candidates
+    return p
+
+
+class Plan:
+    """One search configuration on one device; owns the template bank."""
+
+    def __init__(self, params: Params, device: int = 0, build_templates: bool = True, stream=None):
+        self.params = params
+        h = ctypes.c_void_p()
+        _check(lib().jerk_plan_create(ctypes.byref(params), device, ctypes.byref(h)), "jerk_plan_create")
+        self._h = h
+        self.device = device
+        self.info = Info()
+        _check(lib().jerk_plan_info(self._h, ctypes.byref(self.info)), "jerk_plan_info")
+        if build_templates:
+            self.templates(stream)
+
+    # -- lifecycle --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().jerk_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- the path ---------------------------------------------------------
+    def templates(self, stream=None):
+        _check(lib().jerk_templates(self._h, _stream_handle(stream)), "jerk_templates")
+
+    def search(self, spec, stream=None):
+        """Enqueue a search of a complex64 CUDA tensor (no host sync)."""
+        assert spec.is_cuda and spec.is_contiguous() and str(spec.dtype) == "torch.complex64"
+        _check(lib().jerk_search(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(),
+                                 _stream_handle(stream)), "jerk_search")
+
+    def search_host(self, spec: np.ndarray, stream=None):
+        """Enqueue a search of a host complex64 array (copied by the library)."""
+        a = np.ascontiguousarray(spec, dtype=np.complex64)
+        self._host_ref = a
+        _check(lib().jerk_search_host(self._h, a.ctypes.data_as(ctypes.c_void_p), a.size,
+                                      _stream_handle(stream)), "jerk_search_host")
+
+    def candidates(self, cap: int | None = None):
+        """Synchronise and return the candidates as a list of tuples
+        (stage, p, t, power) sorted by (stage, p), plus the records."""
+        if cap is None:
+            cap = int(self.params.max_candidates)
+        buf = (Candidate * max(cap, 1))()
+        n = ctypes.c_int64()
+        code = lib().jerk_candidates(self._h, buf, cap, ctypes.byref(n))
+        if code not in (JERK_OK, JERK_EOVERFLOW):
+            _check(code, "jerk_candidates")
+        if code == JERK_EOVERFLOW:
+            raise JerkError(code, "jerk_candidates (%d found)" % n.value)
+        return [buf[i] for i in range(n.value)]
+
+    def stats(self):
+        k = int(self.params.n_stages)
+        mu = (ctypes.c_double * k)()
+        sd = (ctypes.c_double * k)()
+        th = (ctypes.c_float * k)()
+        _check(lib().jerk_stats(self._h, mu, sd, th), "jerk_stats")
+        return list(mu), list(sd), list(th)
+
+    # -- single steps -----------------------------------------------------
+    def normalise(self, spec_in, spec_out, stream=None):
+        _check(lib().jerk_normalise(self._h, ctypes.c_void_p(spec_in.data_ptr()), spec_in.numel(),
+                                    ctypes.c_void_p(spec_out.data_ptr()), _stream_handle(stream)),
+               "jerk_normalise")
+
+    def taps(self, t0: int, nt: int, out, stream=None):
+        """out: complex128 CUDA tensor [nt, K]."""
+        _check(lib().jerk_taps(self._h, t0, nt, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "jerk_taps")
+
+    def plane(self, spec, t0: int, nt: int, out, stream=None):
+        """out: float32 CUDA tensor [nt, 2 n]."""
+        _check(lib().jerk_plane(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(), t0, nt,
+                                ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "jerk_plane")
+
+    def maxproj_ptr(self, stage_idx: int):
+        ptr = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        _check(lib().jerk_maxproj(self._h, stage_idx, ctypes.byref(ptr), ctypes.byref(n)), "jerk_maxproj")
+        return ptr.value, n.value
+
+    def maxproj(self, stage_idx: int):
+        """Copy the packed stage max-projection to host: (float32 M, int64 t)."""
+        import torch
+        ptr, n = self.maxproj_ptr(stage_idx)
+        dev = torch.as_tensor(_DevArray(ptr, n, "<u8"), device="cuda:%d" % self.device)
+        torch.cuda.synchronize(self.device)
+        host = dev.cpu().numpy().view(np.uint64)
+        M = (host >> np.uint64(32)).astype(np.uint32).view(np.float32)
+        t = (np.uint64(0xFFFFFFFF) - (host & np.uint64(0xFFFFFFFF))).astype(np.int64)
+        return M, t
+
+
+class _DevArray:
+    """A read-only view of library-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
+                                         "data": (ptr, True), "version": 3}
