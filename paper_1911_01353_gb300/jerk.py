@@ -220,7 +220,7 @@ class Plan:
         """Copy the packed stage max-projection to host: (float32 M, int64 t)."""
         import torch
         ptr, n = self.maxproj_ptr(stage_idx)
-        dev = torch.as_tensor(_DevArray(ptr, n, "<u8"), device="cuda:%d" % self.device)
+        dev = torch.as_tensor(_DevArray(ptr, n, "<i8"), device="cuda:%d" % self.device)
         torch.cuda.synchronize(self.device)
         host = dev.cpu().numpy().view(np.uint64)
         M = (host >> np.uint64(32)).astype(np.uint32).view(np.float32)
@@ -233,4 +233,4 @@ class _DevArray:
 
     def __init__(self, ptr: int, n: int, typestr: str):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,
-                                         "data": (ptr, True), "version": 3}
+                                         "data": (ptr, False), "version": 3}
