@@ -178,6 +178,19 @@ jerk_status jerk_maxproj(jerk_plan plan, int32_t stage_idx, const uint64_t **d_o
  * the FP32 threshold applied.  Arrays of n_stages entries; any may be NULL. */
 jerk_status jerk_stats(jerk_plan plan, double *h_mean, double *h_std, float *h_theta);
 
+/* ---- per-stage timing (the paper's run-time breakdown, Sec. 3 / Fig. 3) ---- */
+
+enum { JERK_N_PHASES = 5 };   /* normalise, conv (fused filter + stage-1), harmonic, stats, peaks */
+
+/* Enable (1) or disable (0) CUDA-event timing of the phases of each
+ * jerk_search.  Off by default; costs five event records per search. */
+jerk_status jerk_profile(jerk_plan plan, int32_t enable);
+
+/* After a profiled search (synchronises it): milliseconds of each phase, in
+ * the order of the enum above, into h_ms[0 .. min(n, JERK_N_PHASES)-1].
+ * JERK_ESTATE if the last search was not profiled. */
+jerk_status jerk_phase_times(jerk_plan plan, float *h_ms, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

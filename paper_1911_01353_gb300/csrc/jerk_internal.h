@@ -129,5 +129,7 @@ struct jerk_plan_s {
     int64_t last_n = 0;
     bool searched = false;
     cudaEvent_t done = nullptr;
+    bool profile = false, profiled = false;
+    cudaEvent_t ev[JERK_N_PHASES + 1] = {};
     jerk::DevCand *h_cand = nullptr;   // pinned staging for candidates
 };

@@ -166,6 +166,13 @@ void release(jerk_plan_s *pl) {
     cudaFree(pl->d_gl);
     if (pl->h_cand) cudaFreeHost(pl->h_cand);
     if (pl->done) cudaEventDestroy(pl->done);
+    for (auto &e : pl->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// phase marker i of a profiled search
+cudaError_t mark(jerk_plan_s *pl, int i, cudaStream_t st) {
+    return pl->profile ? cudaEventRecord(pl->ev[i], st) : cudaSuccess;
 }
 
 // upload the slot tables for spectra of n bins (synchronous w.r.t. the host buffers)
@@ -457,10 +464,12 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     const bool sigma = pl->prm.thresh_mode == JERK_THRESH_SIGMA;
 
     cudaError_t e;
+    JCHECK(mark(pl, 0, st));
     const float2 *spec = normalised_input(pl, d_spec, n, st, &e);
     JCHECK(e);
     for (int si = 0; si < ns; ++si)
         JCHECK(cudaMemsetAsync(pl->d_M[si], 0, sizeof(unsigned long long) * n_cells(bN, pl->prm.stages[si]), st));
+    JCHECK(mark(pl, 1, st));
 
     // fused overlap-and-save + stage-1 max-projection + harmonic rows
     ConvArgs a;
@@ -486,6 +495,7 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     const int ngroups = (pl->T + a.tpg - 1) / a.tpg;
     const int64_t n1 = (int64_t)a.nseg * ngroups;
     JCHECK(launch_conv(pl->log2L, 0, sigma, a, ngroups, st));
+    JCHECK(mark(pl, 2, st));
 
     // harmonic sums for stages > 1
     int64_t nH = 0;
@@ -516,11 +526,13 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
             counts[si] = (double)nf * h.n_cells[si];
         }
     }
+    JCHECK(mark(pl, 3, st));
     JCHECK(cudaMemcpyAsync(pl->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, st));
     JCHECK(launch_finalise_stats(pl->d_stat_part, n1, partH, nH, ns, pl->d_counts, pl->d_thresh,
                                  pl->prm.thresh_mode, pl->d_stats, pl->d_theta, st));
 
     // peaks
+    JCHECK(mark(pl, 4, st));
     JCHECK(cudaMemsetAsync(pl->d_count, 0, sizeof(unsigned long long), st));
     PeakArgs pk;
     std::memset(&pk, 0, sizeof(pk));
@@ -534,9 +546,11 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     pk.cap = pl->prm.max_candidates;
     pk.count = pl->d_count;
     JCHECK(launch_peaks(pk, st));
+    JCHECK(mark(pl, 5, st));
     JCHECK(cudaEventRecord(pl->done, st));
     pl->last_n = n;
     pl->searched = true;
+    pl->profiled = pl->profile;
     return JERK_OK;
 }
 
@@ -590,6 +604,24 @@ jerk_status jerk_maxproj(jerk_plan pl, int32_t stage_idx, const uint64_t **d_out
     if (!pl->searched) return JERK_ESTATE;
     *d_out = (const uint64_t *)pl->d_M[stage_idx];
     *n_cells_out = n_cells((int64_t)pl->b * pl->last_n, pl->prm.stages[stage_idx]);
+    return JERK_OK;
+}
+
+jerk_status jerk_profile(jerk_plan pl, int32_t enable) {
+    if (!pl) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(pl->device));
+    if (enable && !pl->ev[0])
+        for (auto &e : pl->ev) JCHECK(cudaEventCreate(&e));
+    pl->profile = enable != 0;
+    return JERK_OK;
+}
+
+jerk_status jerk_phase_times(jerk_plan pl, float *h_ms, int32_t n) {
+    if (!pl || !h_ms || n < 0) return JERK_EINVAL;
+    if (!pl->searched || !pl->profiled) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    JCHECK(cudaEventSynchronize(pl->done));
+    for (int i = 0; i < n && i < JERK_N_PHASES; ++i) JCHECK(cudaEventElapsedTime(h_ms + i, pl->ev[i], pl->ev[i + 1]));
     return JERK_OK;
 }
 

@@ -21,7 +21,9 @@ THRESH_ABS, THRESH_SIGMA = 0, 1
 # Every function the header declares (kept in step with include/jerk.h).
 EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host",
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
-           "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats")
+           "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
+           "jerk_profile", "jerk_phase_times")
+PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
 class Params(ctypes.Structure):
@@ -78,6 +80,8 @@ def lib() -> ctypes.CDLL:
             "jerk_maxproj": ([vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i64)], st),
             "jerk_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_float)], st),
+            "jerk_profile": ([vp, i32], st),
+            "jerk_phase_times": ([vp, ctypes.POINTER(ctypes.c_float), i32], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -193,6 +197,15 @@ class Plan:
         th = (ctypes.c_float * k)()
         _check(lib().jerk_stats(self._h, mu, sd, th), "jerk_stats")
         return list(mu), list(sd), list(th)
+
+    def profile(self, enable: bool = True):
+        _check(lib().jerk_profile(self._h, 1 if enable else 0), "jerk_profile")
+
+    def phase_times(self):
+        """{phase: ms} of the last profiled search."""
+        ms = (ctypes.c_float * len(PHASES))()
+        _check(lib().jerk_phase_times(self._h, ms, len(PHASES)), "jerk_phase_times")
+        return dict(zip(PHASES, list(ms)))
 
     # -- single steps -----------------------------------------------------
     def normalise(self, spec_in, spec_out, stream=None):
