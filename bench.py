@@ -49,12 +49,14 @@ def args_():
     ap.add_argument("--workload", choices=("paper", "small"), default="paper")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seg-len", type=int, default=0)
+    ap.add_argument("--bins", type=int, default=1 << 22,
+                    help="spectrum length of the paper-scale bank (smaller for profiling)")
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, bins=1 << 22):
     import synth
-    return synth.paper_scale() if name == "paper" else synth.small_single()
+    return synth.paper_scale(bins) if name == "paper" else synth.small_single()
 
 
 def peaks_file():
@@ -191,7 +193,7 @@ def oracle_sample(wl, spec, budget_s=12.0, stride=16, cells=65536):
 
 def reference_arm(a):
     import synth  # noqa: F401
-    wl = workload(a.workload)
+    wl = workload(a.workload, a.bins)
     spec = wl.make()
     times, cells = [], 0
     for i in range(a.warmup + a.steps):
@@ -240,7 +242,7 @@ def main():
     torch.cuda.set_device(local)
 
     import synth
-    wl = workload(a.workload)
+    wl = workload(a.workload, a.bins)
     spec = synth.spectrum(wl.n_bins, wl.seed + 1000 * rank, wl.signals) if rank else wl.make()
     p = pkg.make_params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages,
                         thresh=SIGMA_T[:len(wl.stages)], thresh_mode=pkg.THRESH_SIGMA,

@@ -1,17 +1,23 @@
-// Fused overlap-and-save matched filtering (Sec. 2, Fig. 1): per CTA one
-// segment of the spread spectrum and a group of templates.
+// Fused overlap-and-save matched filtering (Sec. 2, Fig. 1).
 //
-//   1. forward FFT of the segment (once per CTA, kept in shared memory);
-//   2. per template: pointwise multiply by the template spectrum (read from
-//      the L2-resident group slice of the bank), inverse FFT in registers and
-//      shared memory, drop the K-1 overlap, |.|^2;
+// One CTA holds SEGS segments of the spread spectrum (one per group of NT
+// threads) and walks a group of templates:
+//   1. forward FFT of each segment (once per CTA, kept in shared memory);
+//   2. per template: the template spectrum is staged into shared memory by a
+//      TMA bulk copy (cp.async.bulk + mbarrier) issued during the previous
+//      template's transform and shared by the SEGS segments; pointwise
+//      multiply, inverse FFT in registers and padded shared memory, drop the
+//      K-1 overlap, |.|^2;
 //   3. epilogue in registers: running (max, argmax) per cell over the group
 //      -> one packed 64-bit atomicMax per cell into the stage-1
-//      max-projection; FP32/FP64 statistics (SIGMA mode); the harmonic rows
-//      the harmonic sum needs are staged through shared memory and written
+//      max-projection; statistics (SIGMA mode); the harmonic rows the
+//      harmonic sum needs are staged through shared memory and written
 //      coalesced.  In plane mode the power rows are written instead.
 //
-// The power plane is never materialised in search mode.
+// The power plane is never materialised in search mode.  The only wait on
+// another agent is the mbarrier of the bulk copy; it is bounded (about one
+// second of %globaltimer) and on expiry the CTA records an error flag that
+// the host reports as JERK_ETIMEOUT.
 #include "fft.cuh"
 #include "jerk_internal.h"
 
@@ -21,20 +27,92 @@ namespace jerk {
 // digit-reversed writes and 3-way for strided harmonic reads)
 __device__ __forceinline__ int swzf(int a) { return a ^ ((a >> 5) & 31); }
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one elected thread: expect `bytes` and start the bulk global -> shared copy
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for phase `parity` of `bar`, giving up after ~1 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > 1000000000ull) return false;
+    return true;
+}
+
+template <int LOG2L>
+struct ConvCfg {
+    static constexpr int L = 1 << LOG2L;
+    static constexpr int NT = L / 16;
+    static constexpr int SEGS = LOG2L >= 13 ? 1 : 2;          // segments per CTA
+    static constexpr int THREADS = SEGS * NT;
+    static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;
+    static constexpr int WPAD = L + L / 16;                   // padded transpose buffer
+    // dynamic shared memory: template | SEGS x segment spectrum | SEGS x work
+    static constexpr size_t SMEM = sizeof(float2) * ((size_t)L + (size_t)SEGS * L + (size_t)SEGS * WPAD);
+};
+
 template <int LOG2L, int MODE, bool STATS>
-__global__ void __launch_bounds__(FftCfg<LOG2L>::NT)
+__global__ void __launch_bounds__(ConvCfg<LOG2L>::THREADS, ConvCfg<LOG2L>::MINB)
 conv_kernel(ConvArgs a) {
     using C = FftCfg<LOG2L>;
-    constexpr int L = C::L, NT = C::NT;
-    extern __shared__ float2 smem[];
-    float2 *xs = smem;            // segment spectrum, swizzled
-    float2 *work = smem + L;      // transposes / staged power row
+    using CC = ConvCfg<LOG2L>;
+    constexpr int L = C::L, NT = C::NT, SEGS = CC::SEGS;
+    extern __shared__ __align__(128) float2 smem[];
+    float2 *tsm = smem;                                       // staged template spectrum
+    __shared__ __align__(8) uint64_t mbar;
     __shared__ double red[2][32];
 
-    const int j = threadIdx.x;
-    const int s = blockIdx.x;
-    const int64_t seg0 = (int64_t)s * a.V;     // first output cell
-    const int64_t in0 = seg0 - a.bM;           // first spread sample (even)
+    const int tid = threadIdx.x;
+    const int half = tid / NT;                                // which segment of the CTA
+    const int j = tid - half * NT;
+    float2 *xs = smem + L + half * L;                         // segment spectrum, natural order
+    float2 *work = smem + L + SEGS * L + half * CC::WPAD;     // transposes / staged power row
+    const SyncNamed bar_half{1 + half, NT};
+
+    const int s = blockIdx.x * SEGS + half;
+    const int64_t seg0 = (int64_t)s * a.V;                    // first output cell
+    const int64_t in0 = seg0 - a.bM;                          // first spread sample (even)
+
+    int64_t tb = (int64_t)a.t0 + (int64_t)blockIdx.y * a.tpg;
+    int64_t te = tb + a.tpg;
+    if (te > (int64_t)a.t0 + a.nt) te = (int64_t)a.t0 + a.nt;
+
+    if (tid == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (tid == 0 && tb < te) bulk_load(tsm, a.bank + tb * L, (uint32_t)(L * sizeof(float2)), &mbar);
 
     // ---- 1. forward FFT of the spread segment -------------------------------
     float2 v[16];
@@ -43,31 +121,28 @@ conv_kernel(ConvArgs a) {
         twf.init(j);
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
-            const int64_t q = in0 + j + NT * m;          // spread sample index
+            const int64_t q = in0 + j + NT * m;               // spread sample index
             float2 x = make_float2(0.f, 0.f);
             if (((q & 1) == 0) && q >= 0 && (q >> 1) < a.N) x = a.spec[q >> 1];
             v[m] = x;
         }
-        fft_run<LOG2L, -1>(v, work, j, twf);
+        fft_pass0<LOG2L, -1>(v, twf);
+        fft_store0<LOG2L>(v, work, j);
+        fft_rest<LOG2L, -1>(v, work, j, twf, bar_half);
         const int rv = fft_rev<LOG2L>(j);
 #pragma unroll
-        for (int r = 0; r < 16; ++r) xs[swz(rv + NT * r)] = v[r];
+        for (int r = 0; r < 16; ++r) xs[rv + NT * r] = v[r];
     }
-    __syncthreads();
 
     // ---- 2. templates of this group -----------------------------------------
     FftTw<LOG2L, +1> twi;
     twi.init(j);
     const int rv = fft_rev<LOG2L>(j);
-    int64_t tb = (int64_t)a.t0 + (int64_t)blockIdx.y * a.tpg;
-    int64_t te = tb + a.tpg;
-    if (te > (int64_t)a.t0 + a.nt) te = (int64_t)a.t0 + a.nt;
-
-    bool valid[16];
+    unsigned vmask = 0;
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int cell = rv + NT * r;
-        valid[r] = cell < a.V && seg0 + cell < a.bN;
+        if (cell < a.V && seg0 + cell < a.bN) vmask |= 1u << r;
     }
     float mx[16];
     int am[16];
@@ -79,15 +154,29 @@ conv_kernel(ConvArgs a) {
     double d1 = 0.0, d2 = 0.0;
     float c1 = 0.f, c2 = 0.f;
     int nchunk = 0;
+    uint32_t phase = 0;
 
     for (int64_t t = tb; t < te; ++t) {
-        const float2 *ct = a.bank + t * L;
+        const bool ok = mbar_wait_bounded(&mbar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {                          // B1 (also orders `work` reuse)
+            if (tid == 0) {
+                atomicExch(a.err, 1);
+                mbar_wait_bounded(&mbar, phase ^ 1u);         // let an in-flight copy land
+            }
+            return;
+        }
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int f = j + NT * m;
-            v[m] = cmul(xs[swz(f)], __ldg(ct + f));
+            v[m] = cmul(xs[f], tsm[f]);
         }
-        fft_run<LOG2L, +1>(v, work, j, twi);
+        fft_pass0<LOG2L, +1>(v, twi);
+        __syncthreads();                                      // B2: the template buffer is free
+        if (tid == 0 && t + 1 < te)
+            bulk_load(tsm, a.bank + (t + 1) * L, (uint32_t)(L * sizeof(float2)), &mbar);
+        fft_store0<LOG2L>(v, work, j);
+        fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
 #pragma unroll
         for (int r = 0; r < 16; ++r) P[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
@@ -95,7 +184,7 @@ conv_kernel(ConvArgs a) {
         if constexpr (MODE == 0) {
 #pragma unroll
             for (int r = 0; r < 16; ++r) {
-                if (valid[r] && P[r] > mx[r]) {
+                if (P[r] > mx[r]) {
                     mx[r] = P[r];
                     am[r] = (int)t;
                 }
@@ -104,13 +193,13 @@ conv_kernel(ConvArgs a) {
                 float s1 = 0.f, s2 = 0.f;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
-                    const float q = valid[r] ? P[r] : 0.f;
+                    const float q = (vmask >> r) & 1u ? P[r] : 0.f;
                     s1 += q;
                     s2 = fmaf(q, q, s2);
                 }
                 c1 += s1;
                 c2 += s2;
-                if (++nchunk == 8) {
+                if (++nchunk == 32) {
                     d1 += (double)c1;
                     d2 += (double)c2;
                     c1 = c2 = 0.f;
@@ -120,10 +209,10 @@ conv_kernel(ConvArgs a) {
             const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
             if (e0 < e1) {
                 float *pw = reinterpret_cast<float *>(work);
-                __syncthreads();                       // last pass reads of `work` done
+                bar_half();                                   // last pass reads of `work` done
 #pragma unroll
                 for (int r = 0; r < 16; ++r) pw[swzf(rv + NT * r)] = P[r];
-                __syncthreads();
+                bar_half();
                 for (int e = e0; e < e1; ++e) {
                     const int h = __ldg(a.slot_h + e);
                     const int64_t off = __ldg(a.slot_off + e);
@@ -137,20 +226,20 @@ conv_kernel(ConvArgs a) {
                     for (int64_t p = pf + j; p <= pl; p += NT)
                         a.slots[off + p] = pw[swzf((int)(h * p - seg0))];
                 }
-                // the next fft_run begins with a barrier before reusing `work`
+                // the next template's B1 orders these reads before `work` is reused
             }
         } else {
             float *row = a.plane + (t - a.t0) * a.bN + seg0;
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                if (valid[r]) row[rv + NT * r] = P[r];
+                if ((vmask >> r) & 1u) row[rv + NT * r] = P[r];
         }
     }
 
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            if (valid[r] && tb < te) {
+            if (((vmask >> r) & 1u) && tb < te) {
                 const unsigned long long packed =
                     ((unsigned long long)__float_as_uint(mx[r]) << 32) |
                     (unsigned long long)(0xFFFFFFFFu - (unsigned)am[r]);
@@ -165,14 +254,14 @@ conv_kernel(ConvArgs a) {
                 d1 += __shfl_xor_sync(0xffffffffu, d1, o);
                 d2 += __shfl_xor_sync(0xffffffffu, d2, o);
             }
-            if ((j & 31) == 0) {
-                red[0][j >> 5] = d1;
-                red[1][j >> 5] = d2;
+            if ((tid & 31) == 0) {
+                red[0][tid >> 5] = d1;
+                red[1][tid >> 5] = d2;
             }
             __syncthreads();
-            if (j == 0) {
+            if (tid == 0) {
                 double s1 = 0.0, s2 = 0.0;
-                for (int w = 0; w < NT / 32; ++w) {
+                for (int w = 0; w < CC::THREADS / 32; ++w) {
                     s1 += red[0][w];
                     s2 += red[1][w];
                 }
@@ -184,16 +273,16 @@ conv_kernel(ConvArgs a) {
     }
 }
 
-size_t conv_smem_bytes(int log2L) { return (size_t)2 * ((size_t)1 << log2L) * sizeof(float2); }
+int conv_segs_per_cta(int log2L) { return log2L >= 13 ? 1 : 2; }
 
 template <int LOG2L, int MODE, bool STATS>
 static cudaError_t launch_one(const ConvArgs &a, int ngroups, cudaStream_t st) {
+    using CC = ConvCfg<LOG2L>;
     auto k = conv_kernel<LOG2L, MODE, STATS>;
-    const size_t sm = conv_smem_bytes(LOG2L);
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
     if (e != cudaSuccess) return e;
-    dim3 grid(a.nseg, ngroups);
-    k<<<grid, FftCfg<LOG2L>::NT, sm, st>>>(a);
+    dim3 grid((a.nseg + CC::SEGS - 1) / CC::SEGS, ngroups);
+    k<<<grid, CC::THREADS, CC::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -1,15 +1,16 @@
 // Register/shared-memory FFT building blocks for the fused overlap-and-save
 // kernel (the paper's "shared memory implementation of the FFT", Sec. 2,
 // re-designed for sm_103a: 16 points per thread held in registers, radix-16
-// butterflies in registers, XOR-swizzled shared-memory transposes between
-// passes, no bank conflicts for any pass at L = 1024 .. 8192).
+// butterflies in registers, padded shared-memory transposes between passes,
+// no bank conflicts for any pass at L = 1024 .. 8192).
 //
 // Transform of length L = 2^LOG2L with NT = L/16 threads.  Each thread j
 // enters with x[j + NT m], m = 0..15, in registers and leaves with
 // y[rev(j) + NT r], r = 0..15, where y_v = sum_f x_f exp(SIGN 2 pi i f v / L)
 // (unnormalised; SIGN = +1 inverse, -1 forward) and rev(j) is the
 // mixed-radix digit reversal below.  Decimation in frequency, sub-problem-
-// major storage: after pass s the data are A_s[rho][f] at rho * N_s + f.
+// major storage: after pass s the data are A_s[rho][f] at logical index
+// rho * N_s + f, physical index pad16(logical).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,8 +24,10 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// XOR swizzle for 8-byte elements: conflict-free for every transpose used.
-__device__ __forceinline__ int swz(int a) { return a ^ ((a >> 4) & 15); }
+// Padded shared-memory layout: one spare element after every 16, so that the
+// strided transposes of every pass are free of bank conflicts and every
+// address is a per-thread base plus a compile-time offset.
+__device__ __forceinline__ int pad16(int a) { return a + (a >> 4); }
 
 template <int LOG2L>
 struct FftCfg {
@@ -191,15 +194,15 @@ __device__ __forceinline__ int fft_rev(int j) {
     return acc * C::R0 + t;
 }
 
-// The transform.  `work` is float2[L] shared memory; the call begins with a
-// barrier (so the previous transform's last reads are complete) and leaves
-// `work` free for reuse only after the caller's next barrier.
+// The transform, split so that a caller can interleave other work between
+// pass 0 (registers only) and its shared-memory store.  `work` holds
+// L + L/16 float2 (padded).  `Bar` is the barrier used between passes.
+//
+// pass 0: registers a[m] = x[j + NT m] -> a[i + I0 r] = pass-0 output r of item i
 template <int LOG2L, int SIGN>
-__device__ __forceinline__ void fft_run(float2 (&a)[16], float2 *__restrict__ work, int j,
-                                        const FftTw<LOG2L, SIGN> &tw) {
+__device__ __forceinline__ void fft_pass0(float2 (&a)[16], const FftTw<LOG2L, SIGN> &tw) {
     using C = FftCfg<LOG2L>;
-    constexpr int R0 = C::R0, I0 = C::I0, N0 = C::N0;
-    __syncthreads();
+    constexpr int R0 = C::R0, I0 = C::I0;
 #pragma unroll
     for (int i = 0; i < I0; ++i) {
         float2 b[R0];
@@ -207,27 +210,62 @@ __device__ __forceinline__ void fft_run(float2 (&a)[16], float2 *__restrict__ wo
         for (int k = 0; k < R0; ++k) b[k] = a[i + I0 * k];
         dft_small<SIGN, R0>(b);
         twiddle<R0>(b, tw.t0[i]);
-        const int f1 = j + C::NT * i;
 #pragma unroll
-        for (int r = 0; r < R0; ++r) work[swz(r * N0 + f1)] = b[r];
+        for (int r = 0; r < R0; ++r) a[i + I0 * r] = b[r];
     }
-    int nprev = N0;
+}
+
+template <int LOG2L>
+__device__ __forceinline__ void fft_store0(const float2 (&a)[16], float2 *__restrict__ work, int j) {
+    using C = FftCfg<LOG2L>;
+    constexpr int R0 = C::R0, I0 = C::I0, N0 = C::N0, NT = C::NT;
+    float2 *w = work + pad16(j);
+#pragma unroll
+    for (int i = 0; i < I0; ++i)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) w[((NT * i + r * N0) >> 4) * 17] = a[i + I0 * r];
+}
+
+// passes 1..NP; leaves y[rev(j) + NT r] in a[r]
+template <int LOG2L, int SIGN, class Bar>
+__device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ work, int j,
+                                         const FftTw<LOG2L, SIGN> &tw, Bar bar) {
+    using C = FftCfg<LOG2L>;
+    int nprev = C::N0;
 #pragma unroll
     for (int s = 1; s <= C::NP; ++s) {
         const int ns = nprev / 16;
         const int rho = j / ns, fp = j & (ns - 1);
-        __syncthreads();
+        bar();
+        {
+            const float2 *r = work + pad16(rho * nprev + fp);
+            const int step = ns + (ns >> 4);
 #pragma unroll
-        for (int k = 0; k < 16; ++k) a[k] = work[swz(rho * nprev + fp + ns * k)];
+            for (int k = 0; k < 16; ++k) a[k] = r[k * step];
+        }
         dft16<SIGN>(a);
         if (s < C::NP) {
             twiddle<16>(a, tw.ts[s - 1]);
-            __syncthreads();
+            bar();
+            float2 *w = work + pad16(rho * 16 * ns + fp);
+            const int step = ns + (ns >> 4);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) work[swz((rho * 16 + r) * ns + fp)] = a[r];
+            for (int r = 0; r < 16; ++r) w[r * step] = a[r];
         }
         nprev = ns;
     }
 }
+
+struct SyncAll {
+    __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// named barrier over `n` threads (a multiple of 32)
+struct SyncNamed {
+    int id, n;
+    __device__ __forceinline__ void operator()() const {
+        asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+    }
+};
 
 }  // namespace jerk

@@ -43,6 +43,7 @@ struct ConvArgs {
     const int64_t *slot_len;
     float *slots;
     double *stat_part;       // [gridDim.y][gridDim.x][2]
+    int *err;                // set to 1 when a bounded device wait expires
     // plane mode
     float *plane;            // [nt][bN]
 };
@@ -78,7 +79,7 @@ cudaError_t launch_template_fft(const double2 *taps, int32_t nt, int K, int L, c
 cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st);
 cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int ngroups,
                         cudaStream_t st);
-size_t conv_smem_bytes(int log2L);
+int conv_segs_per_cta(int log2L);
 cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats,
                             cudaStream_t st);
 cudaError_t launch_finalise_stats(const double *part1, int64_t n1, const double *partH, int64_t nH,
@@ -116,6 +117,7 @@ struct jerk_plan_s {
     float *d_theta = nullptr;          // [n_stages] applied thresholds
     jerk::DevCand *d_cand = nullptr;
     unsigned long long *d_count = nullptr;
+    int *d_err = nullptr;              // device error flag (bounded waits)
     double2 *d_gl = nullptr;
     int n_gl = 0;
     int64_t bytes = 0;

@@ -61,76 +61,114 @@ cudaError_t launch_normalise(const float2 *in, float2 *out, int64_t n, int B, cu
 
 // ---------------------------------------------------------------------------
 // Harmonic sum (Sec. 3 names it; S_H(p, z, w) = sum_{h=1..H} P(h p, h z, h w)
-// is the reading) and the stage-H max-projection over (z, w).  One thread per
-// fundamental cell p, looping over the fundamentals in ascending t; the
-// harmonic rows P(h p, h z, h w) were written by the fused kernel into
-// per-(h, fundamental) slots indexed by p, so every read is coalesced.  Sums
-// are FP32 in fixed h order; the max keeps the lowest t on ties.
+// is the reading) and the stage-H max-projection over (z, w).  Each thread
+// owns 4 consecutive fundamental cells p and loops over the fundamentals in
+// ascending t; the harmonic rows P(h p, h z, h w) were written by the fused
+// kernel into per-(h, fundamental) slots indexed by p (128-byte aligned), so
+// every read is a coalesced 16-byte load.  Sums are FP32 in fixed h order;
+// the max keeps the lowest t on ties.  HBM-bound: each slot float is read once.
 // ---------------------------------------------------------------------------
+template <int NS>
 __global__ void __launch_bounds__(256) harmonic_kernel(HarmArgs a, bool stats) {
     __shared__ double red[JERK_MAX_STAGES][2][8];
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int top = 0;   // highest stage index defined at this p
-    for (int si = 1; si < a.n_stages; ++si)
-        if (p < a.n_cells[si]) top = si;
-    float mx[JERK_MAX_STAGES];
-    int am[JERK_MAX_STAGES];
-    double d1[JERK_MAX_STAGES], d2[JERK_MAX_STAGES];
-    float c1[JERK_MAX_STAGES], c2[JERK_MAX_STAGES];
+    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    int top = 0;   // highest stage index defined at p0
 #pragma unroll
-    for (int si = 0; si < JERK_MAX_STAGES; ++si) {
-        mx[si] = -1.0f;
-        am[si] = 0;
+    for (int si = 1; si < NS; ++si)
+        if (p0 < a.n_cells[si]) top = si;
+    bool ok[NS][4];
+#pragma unroll
+    for (int si = 1; si < NS; ++si)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) ok[si][c] = p0 + c < a.n_cells[si];
+    float mx[NS][4];
+    int am[NS][4];
+    double d1[NS], d2[NS];
+    float c1[NS], c2[NS];
+#pragma unroll
+    for (int si = 0; si < NS; ++si) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            mx[si][c] = -1.0f;
+            am[si][c] = 0;
+        }
         d1[si] = d2[si] = 0.0;
         c1[si] = c2[si] = 0.f;
+    }
+    int hlo[NS], hhi[NS];
+#pragma unroll
+    for (int si = 1; si < NS; ++si) {
+        hlo[si] = si == 1 ? 1 : a.stages[si - 1] + 1;
+        hhi[si] = a.stages[si];
     }
     const int f0 = blockIdx.y * a.f_chunk;
     const int f1 = min(a.n_fund, f0 + a.f_chunk);
     if (top > 0) {
         int cnt = 0;
+#pragma unroll 2
         for (int f = f0; f < f1; ++f) {
-            const FundEntry &fe = a.fund[f];
-            const int st = min(fe.top_stage, top);
-            float s = 0.f;
-            int h = 1;
+            const FundEntry *fe = a.fund + f;
+            const int t = __ldg(&fe->t);
+            const int st = min(__ldg(&fe->top_stage), top);
+            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int si = 1; si < JERK_MAX_STAGES; ++si) {
-                if (si > st) break;
-                const int H = a.stages[si];
-                for (; h <= H; ++h) s += __ldg(a.slots + fe.off[h - 1] + p);
-                if (s > mx[si]) {
-                    mx[si] = s;
-                    am[si] = fe.t;
-                }
-                if (stats) {
-                    c1[si] += s;
-                    c2[si] = fmaf(s, s, c2[si]);
+            for (int si = 1; si < NS; ++si) {
+                if (si <= st) {
+#pragma unroll
+                    for (int h = 1; h <= JERK_MAX_HARMONIC; ++h) {
+                        if (h >= hlo[si] && h <= hhi[si]) {
+                            const float4 v = __ldg(reinterpret_cast<const float4 *>(
+                                a.slots + __ldg(&fe->off[h - 1]) + p0));
+                            s.x += v.x;
+                            s.y += v.y;
+                            s.z += v.z;
+                            s.w += v.w;
+                        }
+                    }
+                    const float sv[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        if (ok[si][c] && sv[c] > mx[si][c]) {
+                            mx[si][c] = sv[c];
+                            am[si][c] = t;
+                        }
+                        if (stats && ok[si][c]) {
+                            c1[si] += sv[c];
+                            c2[si] = fmaf(sv[c], sv[c], c2[si]);
+                        }
+                    }
                 }
             }
             if (stats && ++cnt == 16) {
                 cnt = 0;
 #pragma unroll
-                for (int si = 1; si < JERK_MAX_STAGES; ++si) {
+                for (int si = 1; si < NS; ++si) {
                     d1[si] += (double)c1[si];
                     d2[si] += (double)c2[si];
                     c1[si] = c2[si] = 0.f;
                 }
             }
         }
-        for (int si = 1; si <= top; ++si) {
-            if (mx[si] >= 0.f) {
-                const unsigned long long packed = ((unsigned long long)__float_as_uint(mx[si]) << 32) |
-                                                  (unsigned long long)(0xFFFFFFFFu - (unsigned)am[si]);
-                if (gridDim.y == 1)
-                    a.M[si][p] = packed;
-                else
-                    atomicMax(a.M[si] + p, packed);
+#pragma unroll
+        for (int si = 1; si < NS; ++si) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (ok[si][c] && mx[si][c] >= 0.f) {
+                    const unsigned long long packed =
+                        ((unsigned long long)__float_as_uint(mx[si][c]) << 32) |
+                        (unsigned long long)(0xFFFFFFFFu - (unsigned)am[si][c]);
+                    if (gridDim.y == 1)
+                        a.M[si][p0 + c] = packed;
+                    else
+                        atomicMax(a.M[si] + p0 + c, packed);
+                }
             }
         }
     }
     if (stats) {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int si = 1; si < a.n_stages; ++si) {
+#pragma unroll
+        for (int si = 1; si < NS; ++si) {
             double x1 = d1[si] + (double)c1[si], x2 = d2[si] + (double)c2[si];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -145,7 +183,7 @@ __global__ void __launch_bounds__(256) harmonic_kernel(HarmArgs a, bool stats) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-            for (int si = 1; si < a.n_stages; ++si) {
+            for (int si = 1; si < NS; ++si) {
                 double s1 = 0.0, s2 = 0.0;
                 for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
                     s1 += red[si][0][w];
@@ -161,7 +199,12 @@ __global__ void __launch_bounds__(256) harmonic_kernel(HarmArgs a, bool stats) {
 cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats, cudaStream_t st) {
     const int64_t nblk = (n_threads + 255) / 256;
     dim3 grid((unsigned)nblk, (unsigned)nblk_y);
-    harmonic_kernel<<<grid, 256, 0, st>>>(a, stats);
+    switch (a.n_stages) {
+        case 2: harmonic_kernel<2><<<grid, 256, 0, st>>>(a, stats); break;
+        case 3: harmonic_kernel<3><<<grid, 256, 0, st>>>(a, stats); break;
+        case 4: harmonic_kernel<4><<<grid, 256, 0, st>>>(a, stats); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

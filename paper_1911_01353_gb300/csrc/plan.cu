@@ -72,7 +72,7 @@ int64_t build_tables(jerk_plan_s *pl, int64_t n, bool fill) {
                 const int64_t len = n_cells(bN, pl->prm.stages[sn]);
                 fe.off[h - 1] = off;
                 if (fill) ents.push_back({index_of(pl, h * pl->zt[t], h * pl->wt[t]), h, off, len});
-                off += len;
+                off += (len + 31) / 32 * 32;   // 128-byte aligned rows (16-byte loads, padded tail)
             }
             if (fill) fund.push_back(fe);
         }
@@ -163,6 +163,7 @@ void release(jerk_plan_s *pl) {
     cudaFree(pl->d_theta);
     cudaFree(pl->d_cand);
     cudaFree(pl->d_count);
+    cudaFree(pl->d_err);
     cudaFree(pl->d_gl);
     if (pl->h_cand) cudaFreeHost(pl->h_cand);
     if (pl->done) cudaEventDestroy(pl->done);
@@ -206,6 +207,17 @@ const float2 *normalised_input(jerk_plan_s *pl, const void *d_spec, int64_t n, c
         return pl->d_spec_norm;
     }
     return (const float2 *)d_spec;
+}
+
+// after a synchronisation point: did a bounded device wait expire?
+jerk_status device_error(jerk_plan_s *pl) {
+    int err = 0;
+    JCHECK(cudaMemcpy(&err, pl->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        cudaMemset(pl->d_err, 0, sizeof(int));
+        return JERK_ETIMEOUT;
+    }
+    return JERK_OK;
 }
 
 }  // namespace
@@ -329,6 +341,8 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     TRY(dalloc(pl, &pl->d_theta, (size_t)JERK_MAX_STAGES));
     TRY(dalloc(pl, &pl->d_cand, (size_t)params->max_candidates));
     TRY(dalloc(pl, &pl->d_count, 1));
+    TRY(dalloc(pl, &pl->d_err, 1));
+    TRY(cudaMemset(pl->d_err, 0, sizeof(int)));
     TRY(dalloc(pl, &pl->d_gl, 64));
     TRY(cudaMallocHost((void **)&pl->h_cand, sizeof(DevCand) * (size_t)params->max_candidates));
     TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
@@ -445,6 +459,7 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
     a.t0 = t0;
     a.nt = nt;
     a.plane = d_out;
+    a.err = pl->d_err;
     const int ngroups = (nt + a.tpg - 1) / a.tpg;
     JCHECK(launch_conv(pl->log2L, 1, false, a, ngroups, st));
     JCHECK(cudaEventRecord(pl->done, st));
@@ -492,8 +507,10 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     a.slot_len = pl->d_slot_len;
     a.slots = pl->d_slots;
     a.stat_part = pl->d_stat_part;
+    a.err = pl->d_err;
     const int ngroups = (pl->T + a.tpg - 1) / a.tpg;
-    const int64_t n1 = (int64_t)a.nseg * ngroups;
+    const int segs = conv_segs_per_cta(pl->log2L);
+    const int64_t n1 = (int64_t)((a.nseg + segs - 1) / segs) * ngroups;
     JCHECK(launch_conv(pl->log2L, 0, sigma, a, ngroups, st));
     JCHECK(mark(pl, 2, st));
 
@@ -516,7 +533,7 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
         }
         h.stat_part = partH;
         h.f_chunk = pl->n_fund;
-        const int64_t nthreads = h.n_cells[1];
+        const int64_t nthreads = (h.n_cells[1] + 3) / 4;   // 4 cells per thread
         nH = (nthreads + 255) / 256;
         JCHECK(launch_harmonic(h, nthreads, 1, sigma, st));
         for (int si = 1; si < ns; ++si) {
@@ -569,6 +586,10 @@ jerk_status jerk_candidates(jerk_plan pl, jerk_candidate *h_out, int64_t cap, in
     if (!pl->searched) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     JCHECK(cudaEventSynchronize(pl->done));
+    {
+        const jerk_status de = device_error(pl);
+        if (de != JERK_OK) return de;
+    }
     unsigned long long cnt = 0;
     JCHECK(cudaMemcpy(&cnt, pl->d_count, sizeof(cnt), cudaMemcpyDeviceToHost));
     const int64_t kept = std::min<int64_t>((int64_t)cnt, pl->prm.max_candidates);
@@ -630,6 +651,10 @@ jerk_status jerk_stats(jerk_plan pl, double *h_mean, double *h_std, float *h_the
     if (!pl->searched) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     JCHECK(cudaEventSynchronize(pl->done));
+    {
+        const jerk_status de = device_error(pl);
+        if (de != JERK_OK) return de;
+    }
     double st[2 * JERK_MAX_STAGES];
     float th[JERK_MAX_STAGES];
     JCHECK(cudaMemcpy(st, pl->d_stats, sizeof(st), cudaMemcpyDeviceToHost));

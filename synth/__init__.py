@@ -119,11 +119,10 @@ def small_single() -> Workload:
                     1 << 16, 20, 2, 60, 20, (1, 2), (15.0, 20.0), 1, [sig])
 
 
-def paper_scale() -> Workload:
-    """2^22 bins, 8 chirps with r, z in [-200, 200], w in [-600, 600] drawn
-    uniformly (SNR uniform in [20, 50]); z in [-200, 200] step 2, w in
+def paper_scale(n: int = 1 << 22) -> Workload:
+    """2^22 bins (or n), 8 chirps with r, z in [-200, 200], w in [-600, 600]
+    drawn uniformly (SNR uniform in [20, 50]); z in [-200, 200] step 2, w in
     [-600, 600] step 20 (12 261 templates); harmonic stages {1, 2, 4, 8}."""
-    n = 1 << 22
     rng = np.random.Generator(np.random.PCG64(2002))
     sigs = []
     for _ in range(8):
@@ -132,7 +131,8 @@ def paper_scale() -> Workload:
                            float(rng.uniform(-600, 600)),
                            float(rng.uniform(20, 50)),
                            float(rng.uniform(0, 2 * math.pi))))
-    return Workload("spectrum 2^22 bins, zmax 200, wmax 600, 12261 templates, stages 1-2-4-8",
+    return Workload("spectrum 2^%d bins, zmax 200, wmax 600, 12261 templates, stages 1-2-4-8"
+                    % int(round(math.log2(n))),
                     n, 200, 2, 600, 20, (1, 2, 4, 8), (20.0, 26.0, 34.0, 48.0), 2, sigs)
 
 
