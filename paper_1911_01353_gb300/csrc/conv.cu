@@ -80,9 +80,38 @@ struct ConvCfg {
     static constexpr int THREADS = SEGS * NT;
     static constexpr int MINB = THREADS >= 512 ? 1 : 512 / THREADS;
     static constexpr int WPAD = L + L / 16;                   // padded transpose buffer
-    // dynamic shared memory: template | SEGS x segment spectrum | SEGS x work
-    static constexpr size_t SMEM = sizeof(float2) * ((size_t)L + (size_t)SEGS * L + (size_t)SEGS * WPAD);
+    static constexpr bool TWS = LOG2L <= 12;                  // twiddles from shared-memory tables
+    static constexpr int TWN = TWS ? twiddle_table_elems<LOG2L>() : 0;
+    static constexpr int NBUF = LOG2L >= 13 ? 1 : 2;          // template buffers in flight
+    // dynamic shared memory: NBUF x template | SEGS x work | twiddle tables | SEGS x argmax (int)
+    static constexpr size_t SMEM =
+        sizeof(float2) * ((size_t)NBUF * L + (size_t)SEGS * WPAD + (size_t)TWN) + sizeof(int) * (size_t)SEGS * L;
 };
+
+// OR of `pred` over the `n` threads of named barrier `id` (also a barrier)
+__device__ __forceinline__ bool named_any(int id, int n, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
+
+template <int LOG2L, int SIGN>
+__device__ __forceinline__ auto make_tw(const float2 *tab, int j) {
+    if constexpr (ConvCfg<LOG2L>::TWS) {
+        return bind_twiddle_tables<LOG2L, SIGN>(tab, j);
+    } else {
+        FftTw<LOG2L, SIGN> tw;
+        tw.init(j);
+        return tw;
+    }
+}
 
 template <int LOG2L, int MODE, bool STATS>
 __global__ void __launch_bounds__(ConvCfg<LOG2L>::THREADS, ConvCfg<LOG2L>::MINB)
@@ -90,16 +119,20 @@ conv_kernel(ConvArgs a) {
     using C = FftCfg<LOG2L>;
     using CC = ConvCfg<LOG2L>;
     constexpr int L = C::L, NT = C::NT, SEGS = CC::SEGS;
+    constexpr int NBUF = CC::NBUF;
     extern __shared__ __align__(128) float2 smem[];
-    float2 *tsm = smem;                                       // staged template spectrum
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t full[NBUF];              // bulk copy of a template landed
+    __shared__ int rel[NBUF];                                 // segments done reading a buffer
+    __shared__ int issued[NBUF];                              // bulk copies issued per buffer
     __shared__ double red[2][32];
 
     const int tid = threadIdx.x;
     const int half = tid / NT;                                // which segment of the CTA
     const int j = tid - half * NT;
-    float2 *xs = smem + L + half * L;                         // segment spectrum, natural order
-    float2 *work = smem + L + SEGS * L + half * CC::WPAD;     // transposes / staged power row
+    float2 *work = smem + NBUF * L + half * CC::WPAD;         // transposes / staged power row
+    float2 *twtab = smem + NBUF * L + SEGS * CC::WPAD;        // twiddle tables (TWS)
+    int *amx = reinterpret_cast<int *>(twtab + CC::TWN) + half * L;   // argmax per cell
+    __shared__ int sbound[SEGS][JERK_MAX_HARMONIC][2];        // per h: first and last p of the segment
     const SyncNamed bar_half{1 + half, NT};
 
     const int s = blockIdx.x * SEGS + half;
@@ -110,15 +143,31 @@ conv_kernel(ConvArgs a) {
     int64_t te = tb + a.tpg;
     if (te > (int64_t)a.t0 + a.nt) te = (int64_t)a.t0 + a.nt;
 
-    if (tid == 0) mbar_init(&mbar, 1);
+    if (tid < NBUF) {
+        mbar_init(&full[tid], 1);
+        rel[tid] = 0;
+        issued[tid] = 0;
+    }
+    if constexpr (CC::TWS) fill_twiddle_tables<LOG2L>(twtab, tid, CC::THREADS);
+    if (j < JERK_MAX_HARMONIC) {
+        // harmonic slots: cells q = h p in [seg0, seg0 + V), q < bN
+        const int64_t h = j + 1;
+        int64_t pl = (seg0 + a.V - 1) / h;
+        const int64_t pmax = (a.bN - 1) / h;
+        sbound[half][j][0] = (int)((seg0 + h - 1) / h);
+        sbound[half][j][1] = (int)(pl < pmax ? pl : pmax);
+    }
     __syncthreads();
-    if (tid == 0 && tb < te) bulk_load(tsm, a.bank + tb * L, (uint32_t)(L * sizeof(float2)), &mbar);
+    if (tid == 0)
+        for (int b = 0; b < NBUF && tb + b < te; ++b) {
+            issued[b] = 1;
+            bulk_load(smem + b * L, a.bank + (tb + b) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+        }
 
     // ---- 1. forward FFT of the spread segment -------------------------------
     float2 v[16];
     {
-        FftTw<LOG2L, -1> twf;
-        twf.init(j);
+        const auto twf = make_tw<LOG2L, -1>(twtab, j);
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int64_t q = in0 + j + NT * m;               // spread sample index
@@ -130,13 +179,18 @@ conv_kernel(ConvArgs a) {
         fft_store0<LOG2L>(v, work, j);
         fft_rest<LOG2L, -1>(v, work, j, twf, bar_half);
         const int rv = fft_rev<LOG2L>(j);
+        bar_half();                                           // all reads of `work` done
 #pragma unroll
-        for (int r = 0; r < 16; ++r) xs[rv + NT * r] = v[r];
+        for (int r = 0; r < 16; ++r) work[rv + NT * r] = v[r];
+        bar_half();
     }
+    // each thread keeps the 16 spectrum values it multiplies: X[j + NT m]
+    float2 xr[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) xr[m] = work[j + NT * m];
 
     // ---- 2. templates of this group -----------------------------------------
-    FftTw<LOG2L, +1> twi;
-    twi.init(j);
+    const auto twi = make_tw<LOG2L, +1>(twtab, j);
     const int rv = fft_rev<LOG2L>(j);
     unsigned vmask = 0;
 #pragma unroll
@@ -145,36 +199,37 @@ conv_kernel(ConvArgs a) {
         if (cell < a.V && seg0 + cell < a.bN) vmask |= 1u << r;
     }
     float mx[16];
-    int am[16];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        mx[r] = -1.0f;
-        am[r] = 0;
-    }
+    for (int r = 0; r < 16; ++r) mx[r] = -1.0f;
     double d1 = 0.0, d2 = 0.0;
     float c1 = 0.f, c2 = 0.f;
     int nchunk = 0;
-    uint32_t phase = 0;
-
+    // Template pipeline: template t sits in buffer b = (t - tb) % NBUF; the
+    // last segment of the CTA to finish reading a buffer refills it with
+    // template t + NBUF, so the segments never wait on each other.
+    bool failed = false;
     for (int64_t t = tb; t < te; ++t) {
-        const bool ok = mbar_wait_bounded(&mbar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {                          // B1 (also orders `work` reuse)
-            if (tid == 0) {
-                atomicExch(a.err, 1);
-                mbar_wait_bounded(&mbar, phase ^ 1u);         // let an in-flight copy land
-            }
-            return;
+        const int it = (int)(t - tb);
+        const int b = it % NBUF;
+        const float2 *tsm = smem + b * L;
+        const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(it / NBUF) & 1u);
+        if (named_any(1 + half, NT, !ok)) {                   // also orders reuse of `work`
+            if (j == 0) atomicExch(a.err, 1);
+            failed = true;
+            break;
         }
 #pragma unroll
-        for (int m = 0; m < 16; ++m) {
-            const int f = j + NT * m;
-            v[m] = cmul(xs[f], tsm[f]);
-        }
+        for (int m = 0; m < 16; ++m) v[m] = cmul(xr[m], tsm[j + NT * m]);
         fft_pass0<LOG2L, +1>(v, twi);
-        __syncthreads();                                      // B2: the template buffer is free
-        if (tid == 0 && t + 1 < te)
-            bulk_load(tsm, a.bank + (t + 1) * L, (uint32_t)(L * sizeof(float2)), &mbar);
+        bar_half();                                           // this segment is done with the buffer
+        if (j == 0) __threadfence_block();
+        if (j == 0 && atomicAdd(&rel[b], 1) == SEGS - 1) {
+            rel[b] = 0;
+            if (t + NBUF < te) {
+                issued[b] += 1;
+                bulk_load(smem + b * L, a.bank + (t + NBUF) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+            }
+        }
         fft_store0<LOG2L>(v, work, j);
         fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
@@ -186,16 +241,24 @@ conv_kernel(ConvArgs a) {
             for (int r = 0; r < 16; ++r) {
                 if (P[r] > mx[r]) {
                     mx[r] = P[r];
-                    am[r] = (int)t;
+                    amx[rv + NT * r] = (int)t;                // rare after the first templates
                 }
             }
             if constexpr (STATS) {
                 float s1 = 0.f, s2 = 0.f;
+                if (vmask == 0xFFFFu) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
-                    const float q = (vmask >> r) & 1u ? P[r] : 0.f;
-                    s1 += q;
-                    s2 = fmaf(q, q, s2);
+                    for (int r = 0; r < 16; ++r) {
+                        s1 += P[r];
+                        s2 = fmaf(P[r], P[r], s2);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        const float q = (vmask >> r) & 1u ? P[r] : 0.f;
+                        s1 += q;
+                        s2 = fmaf(q, q, s2);
+                    }
                 }
                 c1 += s1;
                 c2 += s2;
@@ -213,18 +276,14 @@ conv_kernel(ConvArgs a) {
 #pragma unroll
                 for (int r = 0; r < 16; ++r) pw[swzf(rv + NT * r)] = P[r];
                 bar_half();
+                const int s0 = (int)seg0;
                 for (int e = e0; e < e1; ++e) {
                     const int h = __ldg(a.slot_h + e);
-                    const int64_t off = __ldg(a.slot_off + e);
-                    const int64_t len = __ldg(a.slot_len + e);
-                    // cells q = h p in [seg0, seg0 + V) with q < bN and p < len
-                    const int64_t pf = (seg0 + h - 1) / h;
-                    int64_t pl = (seg0 + a.V - 1) / h;
-                    const int64_t pmax = (a.bN - 1) / h;
-                    if (pl > pmax) pl = pmax;
-                    if (pl > len - 1) pl = len - 1;
-                    for (int64_t p = pf + j; p <= pl; p += NT)
-                        a.slots[off + p] = pw[swzf((int)(h * p - seg0))];
+                    float *dst = a.slots + __ldg(a.slot_off + e);
+                    const int len = (int)__ldg(a.slot_len + e);
+                    const int pf = sbound[half][h - 1][0];
+                    const int pl = min(sbound[half][h - 1][1], len - 1);
+                    for (int p = pf + j; p <= pl; p += NT) dst[p] = pw[swzf(h * p - s0)];
                 }
                 // the next template's B1 orders these reads before `work` is reused
             }
@@ -236,13 +295,19 @@ conv_kernel(ConvArgs a) {
         }
     }
 
+    __syncthreads();
+    if (tid == 0) {
+        // never leave with a bulk copy still writing into this CTA's shared memory
+        for (int b = 0; b < NBUF; ++b)
+            if (issued[b] > 0) mbar_wait_bounded(&full[b], (uint32_t)(issued[b] - 1) & 1u);
+    }
     if constexpr (MODE == 0) {
 #pragma unroll
         for (int r = 0; r < 16; ++r) {
-            if (((vmask >> r) & 1u) && tb < te) {
+            if (((vmask >> r) & 1u) && tb < te && !failed) {
                 const unsigned long long packed =
                     ((unsigned long long)__float_as_uint(mx[r]) << 32) |
-                    (unsigned long long)(0xFFFFFFFFu - (unsigned)am[r]);
+                    (unsigned long long)(0xFFFFFFFFu - (unsigned)amx[rv + NT * r]);
                 atomicMax(a.M1 + seg0 + rv + NT * r, packed);
             }
         }

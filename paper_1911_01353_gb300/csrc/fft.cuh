@@ -162,7 +162,8 @@ __device__ __forceinline__ float2 unit_root(int num, int den) {
     return make_float2(c, SIGN > 0 ? s : -s);
 }
 
-// Per-thread twiddle bases, constant across transforms.
+// Per-thread twiddle bases, constant across transforms; the factors of a
+// pass are generated by a running product (registers only).
 template <int LOG2L, int SIGN>
 struct FftTw {
     using C = FftCfg<LOG2L>;
@@ -179,7 +180,89 @@ struct FftTw {
             nprev = ns;
         }
     }
+    template <int R>
+    __device__ __forceinline__ void apply0(float2 *b, int i) const { twiddle<R>(b, t0[i]); }
+    __device__ __forceinline__ void applys(float2 *a, int s) const { twiddle<16>(a, ts[s - 1]); }
 };
+
+// Twiddle factors read from tables in shared memory (built once per CTA by
+// twiddle_tables below), for the inverse (SIGN = +1) or, conjugated, the
+// forward transform.  Table 0: w_L^{f1 r} at [(r-1) * N0 + f1];
+// table s (1..NP-1): w_{N_{s-1}}^{f' r} at [(r-1) * N_s + f'].
+template <int LOG2L, int SIGN>
+struct FftTwSmem {
+    using C = FftCfg<LOG2L>;
+    const float2 *t0;
+    const float2 *ts[C::NP > 1 ? C::NP - 1 : 1];
+    int j;
+    __device__ __forceinline__ static float2 cj(float2 w) { return SIGN > 0 ? w : make_float2(w.x, -w.y); }
+    template <int R>
+    __device__ __forceinline__ void apply0(float2 *b, int i) const {
+        const float2 *p = t0 + j + C::NT * i;
+#pragma unroll
+        for (int r = 1; r < R; ++r) b[r] = cmul(b[r], cj(p[(r - 1) * C::N0]));
+    }
+    __device__ __forceinline__ void applys(float2 *a, int s) const {
+        int ns = C::N0;
+#pragma unroll
+        for (int q = 0; q < s; ++q) ns /= 16;
+        const float2 *p = ts[s - 1] + (j & (ns - 1));
+#pragma unroll
+        for (int r = 1; r < 16; ++r) a[r] = cmul(a[r], cj(p[(r - 1) * ns]));
+    }
+};
+
+// floats of shared memory the tables of FftTwSmem need
+template <int LOG2L>
+__host__ __device__ constexpr int twiddle_table_elems() {
+    using C = FftCfg<LOG2L>;
+    int n = (C::R0 - 1) * C::N0;
+    int ns = C::N0;
+    for (int s = 1; s < C::NP; ++s) {
+        ns /= 16;
+        n += 15 * ns;
+    }
+    return n;
+}
+
+// fill the tables (inverse sign) with `nthr` cooperating threads
+template <int LOG2L>
+__device__ __forceinline__ void fill_twiddle_tables(float2 *tab, int tid, int nthr) {
+    using C = FftCfg<LOG2L>;
+    for (int e = tid; e < (C::R0 - 1) * C::N0; e += nthr) {
+        const int r = e / C::N0 + 1, f1 = e % C::N0;
+        tab[e] = unit_root<+1>((f1 * r) & (C::L - 1), C::L);
+    }
+    float2 *p = tab + (C::R0 - 1) * C::N0;
+    int nprev = C::N0;
+#pragma unroll
+    for (int s = 1; s < C::NP; ++s) {
+        const int ns = nprev / 16;
+        for (int e = tid; e < 15 * ns; e += nthr) {
+            const int r = e / ns + 1, fp = e % ns;
+            p[e] = unit_root<+1>((fp * r) & (nprev - 1), nprev);
+        }
+        p += 15 * ns;
+        nprev = ns;
+    }
+}
+
+template <int LOG2L, int SIGN>
+__device__ __forceinline__ FftTwSmem<LOG2L, SIGN> bind_twiddle_tables(const float2 *tab, int j) {
+    using C = FftCfg<LOG2L>;
+    FftTwSmem<LOG2L, SIGN> tw;
+    tw.j = j;
+    tw.t0 = tab;
+    const float2 *p = tab + (C::R0 - 1) * C::N0;
+    int ns = C::N0;
+#pragma unroll
+    for (int s = 1; s < C::NP; ++s) {
+        ns /= 16;
+        tw.ts[s - 1] = p;
+        p += 15 * ns;
+    }
+    return tw;
+}
 
 // digit reversal: thread j's outputs sit at rev(j) + NT r
 template <int LOG2L>
@@ -199,8 +282,8 @@ __device__ __forceinline__ int fft_rev(int j) {
 // L + L/16 float2 (padded).  `Bar` is the barrier used between passes.
 //
 // pass 0: registers a[m] = x[j + NT m] -> a[i + I0 r] = pass-0 output r of item i
-template <int LOG2L, int SIGN>
-__device__ __forceinline__ void fft_pass0(float2 (&a)[16], const FftTw<LOG2L, SIGN> &tw) {
+template <int LOG2L, int SIGN, class Tw>
+__device__ __forceinline__ void fft_pass0(float2 (&a)[16], const Tw &tw) {
     using C = FftCfg<LOG2L>;
     constexpr int R0 = C::R0, I0 = C::I0;
 #pragma unroll
@@ -209,7 +292,7 @@ __device__ __forceinline__ void fft_pass0(float2 (&a)[16], const FftTw<LOG2L, SI
 #pragma unroll
         for (int k = 0; k < R0; ++k) b[k] = a[i + I0 * k];
         dft_small<SIGN, R0>(b);
-        twiddle<R0>(b, tw.t0[i]);
+        tw.template apply0<R0>(b, i);
 #pragma unroll
         for (int r = 0; r < R0; ++r) a[i + I0 * r] = b[r];
     }
@@ -227,9 +310,9 @@ __device__ __forceinline__ void fft_store0(const float2 (&a)[16], float2 *__rest
 }
 
 // passes 1..NP; leaves y[rev(j) + NT r] in a[r]
-template <int LOG2L, int SIGN, class Bar>
-__device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ work, int j,
-                                         const FftTw<LOG2L, SIGN> &tw, Bar bar) {
+template <int LOG2L, int SIGN, class Tw, class Bar>
+__device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ work, int j, const Tw &tw,
+                                         Bar bar) {
     using C = FftCfg<LOG2L>;
     int nprev = C::N0;
 #pragma unroll
@@ -245,7 +328,7 @@ __device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ w
         }
         dft16<SIGN>(a);
         if (s < C::NP) {
-            twiddle<16>(a, tw.ts[s - 1]);
+            tw.applys(a, s);
             bar();
             float2 *w = work + pad16(rho * 16 * ns + fp);
             const int step = ns + (ns >> 4);
