@@ -191,6 +191,32 @@ jerk_status jerk_profile(jerk_plan plan, int32_t enable);
  * JERK_ESTATE if the last search was not profiled. */
 jerk_status jerk_phase_times(jerk_plan plan, float *h_ms, int32_t n);
 
+/* ---- candidate extraction without allocation (no counterpart in the paper) ----
+ *
+ * For callers that cannot allocate device memory at the point where they
+ * extract candidates: a real-time stage that reserved all its memory before
+ * observing started (an allocation there can synchronise the device), or a
+ * program whose device memory belongs to another allocator.  It applies the
+ * library's peak rule to one stage-H max-projection (the array jerk_maxproj
+ * returns: n_cells packed entries (float bits << 32) | (0xFFFFFFFF - t)):
+ * a cell p is kept when M(p) > theta, M(p) > M(p-1) and M(p) >= M(p+1), a
+ * missing neighbour counting as -inf.  Kept cells are written in increasing
+ * p to d_out (device, capacity cap records; r = p/2, z/w from the grid given
+ * by zmax, dz, wmax, dw; stage = H) and their number to *d_count (device
+ * int64; it may exceed cap, and then only the first cap are written).
+ *
+ * Nothing is allocated: the scratch (per-block counts and offsets) is a
+ * fixed 512 KiB array inside the library that each GPU using the library
+ * holds until the process exits.  n_cells above 2^27 is rejected with
+ * JERK_EINVAL.  All calls share that array: calls that may overlap on a GPU
+ * (other streams or host threads) race and must be serialised by the caller.
+ * The first call on a device looks up the array's device address with that
+ * device current; make it before starting any CUDA stream capture.
+ * Enqueued on `stream` on the current device; no host synchronisation. */
+jerk_status jerk_peaks_noalloc(const uint64_t *d_maxproj, int64_t n_cells, float theta, int32_t stage,
+                               int32_t zmax, int32_t dz, int32_t wmax, int32_t dw,
+                               jerk_candidate *d_out, int64_t cap, int64_t *d_count, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,7 @@ THRESH_ABS, THRESH_SIGMA = 0, 1
 EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host",
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
-           "jerk_profile", "jerk_phase_times")
+           "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
                             ctypes.POINTER(ctypes.c_float)], st),
             "jerk_profile": ([vp, i32], st),
             "jerk_phase_times": ([vp, ctypes.POINTER(ctypes.c_float), i32], st),
+            "jerk_peaks_noalloc": ([vp, i64, ctypes.c_float, i32, i32, i32, i32, i32, vp, i64, vp, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -125,6 +126,20 @@ def make_params(zmax, dz, wmax, dw, stages=(1, 2), thresh=(15.0, 20.0), thresh_m
     p.norm_block, p.precision = norm_block, precision
     p.max_bins, p.max_candidates = max_bins, max_candidates
     return p
+
+
+CANDIDATE_DTYPE = np.dtype([("p", "<i8"), ("r", "<f8"), ("t", "<i4"), ("z_idx", "<i4"), ("w_idx", "<i4"),
+                            ("stage", "<i4"), ("z", "<f4"), ("w", "<f4"), ("power", "<f4"),
+                            ("reserved", "<i4")])
+
+
+def peaks_noalloc(d_maxproj: int, n_cells: int, theta: float, stage: int, zmax: int, dz: int, wmax: int,
+                  dw: int, d_out: int, cap: int, d_count: int, stream=None):
+    """Candidate extraction that allocates no device memory (device pointers in
+    and out; see ``jerk_peaks_noalloc`` in include/jerk.h)."""
+    _check(lib().jerk_peaks_noalloc(ctypes.c_void_p(d_maxproj), n_cells, theta, stage, zmax, dz, wmax, dw,
+                                    ctypes.c_void_p(d_out), cap, ctypes.c_void_p(d_count),
+                                    _stream_handle(stream)), "jerk_peaks_noalloc")
 
 
 class Plan:
