@@ -306,12 +306,9 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
 
-    total_ms = sum(step_ms)
-    e2e_total = sum(e2e_ms)
-    if dist:
-        t = torch.tensor([total_ms, e2e_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_total = float(t[0]), float(t[1])
+    from paper_1911_01353_gb300.ranks import max_over_ranks
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
+    e2e_total = max_over_ranks(sum(e2e_ms), dist, "cuda")
 
     value = world * cells * a.steps / (total_ms / 1e3)
     e2e_value = world * cells * a.steps / (e2e_total / 1e3)
