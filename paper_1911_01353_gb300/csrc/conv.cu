@@ -23,9 +23,10 @@
 
 namespace jerk {
 
-// float swizzle for the staged power row (at most 2-way conflicts for the
-// digit-reversed writes and 3-way for strided harmonic reads)
-__device__ __forceinline__ int swzf(int a) { return a ^ ((a >> 5) & 31); }
+// float swizzle for the staged power row: keeps groups of 4 cells together
+// (16-byte reads of the h = 1 row), at most 2-way conflicts for the
+// digit-reversed writes and 3-way for the h = 2 reads
+__device__ __forceinline__ int swzf(int a) { return a ^ (((a >> 5) & 7) << 2); }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -83,10 +84,23 @@ struct ConvCfg {
     static constexpr bool TWS = LOG2L <= 12;                  // twiddles from shared-memory tables
     static constexpr int TWN = TWS ? twiddle_table_elems<LOG2L>() : 0;
     static constexpr int NBUF = LOG2L >= 13 ? 1 : 2;          // template buffers in flight
-    // dynamic shared memory: NBUF x template | SEGS x work | twiddle tables | SEGS x argmax (int)
-    static constexpr size_t SMEM =
-        sizeof(float2) * ((size_t)NBUF * L + (size_t)SEGS * WPAD + (size_t)TWN) + sizeof(int) * (size_t)SEGS * L;
+    // dynamic shared memory: NBUF x template | SEGS x work | twiddle tables |
+    // SEGS x staged power row (float) | SEGS x argmax offset within the group (uint16)
+    static constexpr size_t SMEM = sizeof(float2) * ((size_t)NBUF * L + (size_t)SEGS * WPAD + (size_t)TWN) +
+                                   sizeof(float) * (size_t)SEGS * L + sizeof(uint16_t) * (size_t)SEGS * L;
 };
+
+// sum of 16 values as a balanced tree (short dependency chains)
+__device__ __forceinline__ float tree16(const float (&x)[16]) {
+    float a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = x[2 * i] + x[2 * i + 1];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = a[2 * i] + a[2 * i + 1];
+    a[0] = a[0] + a[1];
+    a[2] = a[2] + a[3];
+    return a[0] + a[2];
+}
 
 // OR of `pred` over the `n` threads of named barrier `id` (also a barrier)
 __device__ __forceinline__ bool named_any(int id, int n, bool pred) {
@@ -113,6 +127,30 @@ __device__ __forceinline__ auto make_tw(const float2 *tab, int j) {
     }
 }
 
+// Store the staged power row of one template into its harmonic-row slots
+// (entries e0..e1): cells q = h p of this segment, p within the row.
+__device__ __forceinline__ void store_rows(const ConvArgs &a, const float *pw, const int (*sb)[2], int e0, int e1,
+                                           int s0, int j, int NT) {
+    for (int e = e0; e < e1; ++e) {
+        const int h = __ldg(a.slot_h + e);
+        float *dst = a.slots + __ldg(a.slot_off + e);
+        const int len = (int)__ldg(a.slot_len + e);
+        const int pf = sb[h - 1][0];
+        const int pl = min(sb[h - 1][1], len - 1);
+        if (pl < pf) continue;                                // this segment is past the row's end
+        if (h == 1) {
+            // p = seg0 + v: whole groups of 4 (seg0 and V are multiples of 4 and
+            // the row is 128-byte aligned), then the ragged end one by one
+            const int n4 = (pl - pf + 1) >> 2;
+            for (int g = j; g < n4; g += NT)
+                *reinterpret_cast<float4 *>(dst + pf + 4 * g) = *reinterpret_cast<const float4 *>(pw + swzf(4 * g));
+            for (int p = pf + 4 * n4 + j; p <= pl; p += NT) dst[p] = pw[swzf(p - s0)];
+        } else {
+            for (int p = pf + j; p <= pl; p += NT) dst[p] = pw[swzf(h * p - s0)];
+        }
+    }
+}
+
 template <int LOG2L, int MODE, bool STATS>
 __global__ void __launch_bounds__(ConvCfg<LOG2L>::THREADS, ConvCfg<LOG2L>::MINB)
 conv_kernel(ConvArgs a) {
@@ -131,7 +169,9 @@ conv_kernel(ConvArgs a) {
     const int j = tid - half * NT;
     float2 *work = smem + NBUF * L + half * CC::WPAD;         // transposes / staged power row
     float2 *twtab = smem + NBUF * L + SEGS * CC::WPAD;        // twiddle tables (TWS)
-    int *amx = reinterpret_cast<int *>(twtab + CC::TWN) + half * L;   // argmax per cell
+    float *stage = reinterpret_cast<float *>(twtab + CC::TWN) + half * L;   // power row awaiting slot stores
+    uint16_t *amx = reinterpret_cast<uint16_t *>(reinterpret_cast<float *>(twtab + CC::TWN) + SEGS * L) +
+                    half * L;                                  // argmax per cell, as t - tb
     __shared__ int sbound[SEGS][JERK_MAX_HARMONIC][2];        // per h: first and last p of the segment
     const SyncNamed bar_half{1 + half, NT};
 
@@ -208,6 +248,7 @@ conv_kernel(ConvArgs a) {
     // last segment of the CTA to finish reading a buffer refills it with
     // template t + NBUF, so the segments never wait on each other.
     bool failed = false;
+    int pend0 = 0, pend1 = 0;                                 // slot entries of the staged row
     for (int64_t t = tb; t < te; ++t) {
         const int it = (int)(t - tb);
         const int b = it % NBUF;
@@ -231,6 +272,8 @@ conv_kernel(ConvArgs a) {
             }
         }
         fft_store0<LOG2L>(v, work, j);
+        if constexpr (MODE == 0)
+            if (pend0 < pend1) store_rows(a, stage, sbound[half], pend0, pend1, (int)seg0, j, NT);
         fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
 #pragma unroll
@@ -241,27 +284,18 @@ conv_kernel(ConvArgs a) {
             for (int r = 0; r < 16; ++r) {
                 if (P[r] > mx[r]) {
                     mx[r] = P[r];
-                    amx[rv + NT * r] = (int)t;                // rare after the first templates
+                    amx[rv + NT * r] = (uint16_t)it;          // rare after the first templates
                 }
             }
             if constexpr (STATS) {
-                float s1 = 0.f, s2 = 0.f;
-                if (vmask == 0xFFFFu) {
+                float q[16], q2[16];
 #pragma unroll
-                    for (int r = 0; r < 16; ++r) {
-                        s1 += P[r];
-                        s2 = fmaf(P[r], P[r], s2);
-                    }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 16; ++r) {
-                        const float q = (vmask >> r) & 1u ? P[r] : 0.f;
-                        s1 += q;
-                        s2 = fmaf(q, q, s2);
-                    }
+                for (int r = 0; r < 16; ++r) {
+                    q[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                    q2[r] = q[r] * q[r];
                 }
-                c1 += s1;
-                c2 += s2;
+                c1 += tree16(q);
+                c2 += tree16(q2);
                 if (++nchunk == 32) {
                     d1 += (double)c1;
                     d2 += (double)c2;
@@ -269,24 +303,15 @@ conv_kernel(ConvArgs a) {
                     nchunk = 0;
                 }
             }
+            // harmonic rows of this template: stage the power row now, store it
+            // during the next template's transform (whose barriers order it)
             const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
             if (e0 < e1) {
-                float *pw = reinterpret_cast<float *>(work);
-                bar_half();                                   // last pass reads of `work` done
 #pragma unroll
-                for (int r = 0; r < 16; ++r) pw[swzf(rv + NT * r)] = P[r];
-                bar_half();
-                const int s0 = (int)seg0;
-                for (int e = e0; e < e1; ++e) {
-                    const int h = __ldg(a.slot_h + e);
-                    float *dst = a.slots + __ldg(a.slot_off + e);
-                    const int len = (int)__ldg(a.slot_len + e);
-                    const int pf = sbound[half][h - 1][0];
-                    const int pl = min(sbound[half][h - 1][1], len - 1);
-                    for (int p = pf + j; p <= pl; p += NT) dst[p] = pw[swzf(h * p - s0)];
-                }
-                // the next template's B1 orders these reads before `work` is reused
+                for (int r = 0; r < 16; ++r) stage[swzf(rv + NT * r)] = P[r];
             }
+            pend0 = e0;
+            pend1 = e1;
         } else {
             float *row = a.plane + (t - a.t0) * a.bN + seg0;
 #pragma unroll
@@ -295,6 +320,12 @@ conv_kernel(ConvArgs a) {
         }
     }
 
+    if constexpr (MODE == 0) {
+        if (!failed && pend0 < pend1) {
+            bar_half();
+            store_rows(a, stage, sbound[half], pend0, pend1, (int)seg0, j, NT);
+        }
+    }
     __syncthreads();
     if (tid == 0) {
         // never leave with a bulk copy still writing into this CTA's shared memory
@@ -307,7 +338,7 @@ conv_kernel(ConvArgs a) {
             if (((vmask >> r) & 1u) && tb < te && !failed) {
                 const unsigned long long packed =
                     ((unsigned long long)__float_as_uint(mx[r]) << 32) |
-                    (unsigned long long)(0xFFFFFFFFu - (unsigned)amx[rv + NT * r]);
+                    (unsigned long long)(0xFFFFFFFFu - (unsigned)(tb + amx[rv + NT * r]));
                 atomicMax(a.M1 + seg0 + rv + NT * r, packed);
             }
         }
