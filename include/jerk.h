@@ -98,7 +98,11 @@ typedef struct {
     int64_t max_bins;
     int64_t slot_floats;     /* harmonic-row workspace at max_bins, in floats */
     int64_t workspace_bytes; /* device bytes the plan holds */
-    const void *d_bank;      /* complex64[n_templates][L] template spectra (valid after jerk_templates) */
+    int64_t transforms;      /* length-L inverse transforms one search of max_bins bins performs */
+    int32_t n_groups;        /* template groups (similar half-width, own segment length) */
+    int32_t reserved;
+    const void *d_bank;      /* complex64[n_templates][L] template spectra in processing order
+                                (see jerk_template_row; valid after jerk_templates) */
 } jerk_info;
 
 /* Validate `params`, select device `device` (made current), size and
@@ -145,6 +149,14 @@ const char *jerk_status_str(jerk_status status);
 
 /* Fill *info.  Never fails on a valid plan. */
 jerk_status jerk_plan_info(jerk_plan plan, jerk_info *info);
+
+/* Where template t (0 <= t < n_templates) sits in the bank: *row is its row
+ * of d_bank, *tap_offset the offset bM_g of its group (the spectrum of row
+ * `row` is (1/L) sum_m c_{m - bM_g} exp(+2 pi i f m / L), m < 2 bM_g + 1) and
+ * *seg_valid its group's segment length V_g = L - 2 bM_g.  Any output may be
+ * NULL.  Templates are grouped by half-width m(z, w) so that a group of short
+ * filters uses a short overlap. */
+jerk_status jerk_template_row(jerk_plan plan, int32_t t, int32_t *row, int32_t *tap_offset, int32_t *seg_valid);
 
 /* ---- single steps of the path (for parity checks and composition) ---- */
 

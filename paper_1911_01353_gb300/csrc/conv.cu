@@ -1,7 +1,10 @@
 // Fused overlap-and-save matched filtering (Sec. 2, Fig. 1).
 //
 // One CTA holds SEGS segments of the spread spectrum (one per group of NT
-// threads) and walks a group of templates:
+// threads) and walks a group of templates.  Templates are grouped by filter
+// half-width, and each group uses its own overlap (tap offset bM) and hence
+// its own segment length V = L - 2 bM, so short filters waste less of each
+// transform on the overlap:
 //   1. forward FFT of each segment (once per CTA, kept in shared memory);
 //   2. per template: the template spectrum is staged into shared memory by a
 //      TMA bulk copy (cp.async.bulk + mbarrier) issued during the previous
@@ -175,13 +178,14 @@ conv_kernel(ConvArgs a) {
     __shared__ int sbound[SEGS][JERK_MAX_HARMONIC][2];        // per h: first and last p of the segment
     const SyncNamed bar_half{1 + half, NT};
 
-    const int s = blockIdx.x * SEGS + half;
-    const int64_t seg0 = (int64_t)s * a.V;                    // first output cell
-    const int64_t in0 = seg0 - a.bM;                          // first spread sample (even)
-
-    int64_t tb = (int64_t)a.t0 + (int64_t)blockIdx.y * a.tpg;
-    int64_t te = tb + a.tpg;
-    if (te > (int64_t)a.t0 + a.nt) te = (int64_t)a.t0 + a.nt;
+    // template group of this CTA (groups are few; CTAs are group-major)
+    int g = 0;
+    while (g + 1 < a.n_groups && (int)blockIdx.x >= __ldg(&a.grp[g + 1].cta0)) ++g;
+    const int V = __ldg(&a.grp[g].V), bM = __ldg(&a.grp[g].bM);
+    const int64_t tb = __ldg(&a.grp[g].tb), te = __ldg(&a.grp[g].te);
+    const int s = ((int)blockIdx.x - __ldg(&a.grp[g].cta0)) * SEGS + half;
+    const int64_t seg0 = (int64_t)s * V;                      // first output cell
+    const int64_t in0 = seg0 - bM;                            // first spread sample (even)
 
     if (tid < NBUF) {
         mbar_init(&full[tid], 1);
@@ -192,7 +196,7 @@ conv_kernel(ConvArgs a) {
     if (j < JERK_MAX_HARMONIC) {
         // harmonic slots: cells q = h p in [seg0, seg0 + V), q < bN
         const int64_t h = j + 1;
-        int64_t pl = (seg0 + a.V - 1) / h;
+        int64_t pl = (seg0 + V - 1) / h;
         const int64_t pmax = (a.bN - 1) / h;
         sbound[half][j][0] = (int)((seg0 + h - 1) / h);
         sbound[half][j][1] = (int)(pl < pmax ? pl : pmax);
@@ -236,7 +240,7 @@ conv_kernel(ConvArgs a) {
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
         const int cell = rv + NT * r;
-        if (cell < a.V && seg0 + cell < a.bN) vmask |= 1u << r;
+        if (cell < V && seg0 + cell < a.bN) vmask |= 1u << r;
     }
     float mx[16];
 #pragma unroll
@@ -249,8 +253,9 @@ conv_kernel(ConvArgs a) {
     // template t + NBUF, so the segments never wait on each other.
     bool failed = false;
     int pend0 = 0, pend1 = 0;                                 // slot entries of the staged row
-    for (int64_t t = tb; t < te; ++t) {
-        const int it = (int)(t - tb);
+    for (int64_t k = tb; k < te; ++k) {                     // processing index
+        const int it = (int)(k - tb);
+        const int t = __ldg(a.order + k);                     // template index
         const int b = it % NBUF;
         const float2 *tsm = smem + b * L;
         const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(it / NBUF) & 1u);
@@ -266,9 +271,9 @@ conv_kernel(ConvArgs a) {
         if (j == 0) __threadfence_block();
         if (j == 0 && atomicAdd(&rel[b], 1) == SEGS - 1) {
             rel[b] = 0;
-            if (t + NBUF < te) {
+            if (k + NBUF < te) {
                 issued[b] += 1;
-                bulk_load(smem + b * L, a.bank + (t + NBUF) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+                bulk_load(smem + b * L, a.bank + (k + NBUF) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
             }
         }
         fft_store0<LOG2L>(v, work, j);
@@ -312,8 +317,8 @@ conv_kernel(ConvArgs a) {
             }
             pend0 = e0;
             pend1 = e1;
-        } else {
-            float *row = a.plane + (t - a.t0) * a.bN + seg0;
+        } else if (t >= a.t0 && t < a.t0 + a.nt) {
+            float *row = a.plane + (int64_t)(t - a.t0) * a.bN + seg0;
 #pragma unroll
             for (int r = 0; r < 16; ++r)
                 if ((vmask >> r) & 1u) row[rv + NT * r] = P[r];
@@ -338,7 +343,7 @@ conv_kernel(ConvArgs a) {
             if (((vmask >> r) & 1u) && tb < te && !failed) {
                 const unsigned long long packed =
                     ((unsigned long long)__float_as_uint(mx[r]) << 32) |
-                    (unsigned long long)(0xFFFFFFFFu - (unsigned)(tb + amx[rv + NT * r]));
+                    (unsigned long long)(0xFFFFFFFFu - (unsigned)__ldg(a.order + tb + amx[rv + NT * r]));
                 atomicMax(a.M1 + seg0 + rv + NT * r, packed);
             }
         }
@@ -361,7 +366,7 @@ conv_kernel(ConvArgs a) {
                     s1 += red[0][w];
                     s2 += red[1][w];
                 }
-                const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+                const int64_t blk = blockIdx.x;
                 a.stat_part[2 * blk] = s1;
                 a.stat_part[2 * blk + 1] = s2;
             }
@@ -372,30 +377,28 @@ conv_kernel(ConvArgs a) {
 int conv_segs_per_cta(int log2L) { return log2L >= 13 ? 1 : 2; }
 
 template <int LOG2L, int MODE, bool STATS>
-static cudaError_t launch_one(const ConvArgs &a, int ngroups, cudaStream_t st) {
+static cudaError_t launch_one(const ConvArgs &a, int n_ctas, cudaStream_t st) {
     using CC = ConvCfg<LOG2L>;
     auto k = conv_kernel<LOG2L, MODE, STATS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.nseg + CC::SEGS - 1) / CC::SEGS, ngroups);
-    k<<<grid, CC::THREADS, CC::SMEM, st>>>(a);
+    k<<<n_ctas, CC::THREADS, CC::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int LOG2L>
-static cudaError_t launch_L(int mode, bool stats, const ConvArgs &a, int ngroups, cudaStream_t st) {
-    if (mode == 1) return launch_one<LOG2L, 1, false>(a, ngroups, st);
-    if (stats) return launch_one<LOG2L, 0, true>(a, ngroups, st);
-    return launch_one<LOG2L, 0, false>(a, ngroups, st);
+static cudaError_t launch_L(int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st) {
+    if (mode == 1) return launch_one<LOG2L, 1, false>(a, n_ctas, st);
+    if (stats) return launch_one<LOG2L, 0, true>(a, n_ctas, st);
+    return launch_one<LOG2L, 0, false>(a, n_ctas, st);
 }
 
-cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int ngroups,
-                        cudaStream_t st) {
+cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st) {
     switch (log2L) {
-        case 10: return launch_L<10>(mode, stats, a, ngroups, st);
-        case 11: return launch_L<11>(mode, stats, a, ngroups, st);
-        case 12: return launch_L<12>(mode, stats, a, ngroups, st);
-        case 13: return launch_L<13>(mode, stats, a, ngroups, st);
+        case 10: return launch_L<10>(mode, stats, a, n_ctas, st);
+        case 11: return launch_L<11>(mode, stats, a, n_ctas, st);
+        case 12: return launch_L<12>(mode, stats, a, n_ctas, st);
+        case 13: return launch_L<13>(mode, stats, a, n_ctas, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -26,15 +26,22 @@ struct FundEntry {
     int64_t off[JERK_MAX_HARMONIC];   // slot offset (floats) of harmonic h = i + 1
 };
 
+// A group of templates processed together: templates with similar half-width
+// share a tap offset bM and segment length V (processing indices tb..te-1 of
+// the bank); cta0 is the group's first CTA in the launch.
+struct ConvGroup {
+    int32_t tb, te, V, bM, cta0, pad;
+};
+
 // Arguments of the fused overlap-and-save kernel.
 struct ConvArgs {
     const float2 *spec;      // normalised spectrum, N bins
     int64_t N, bN;
-    const float2 *bank;      // [T][L] template spectra
-    int32_t T, tpg;          // templates, templates per group
-    int32_t V, bM;           // outputs kept per segment, overlap offset (b M)
-    int32_t nseg;
-    int32_t t0, nt;          // template range of this launch
+    const float2 *bank;      // [T][L] template spectra in processing order
+    const int32_t *order;    // processing index -> template index t
+    const ConvGroup *grp;    // [n_groups + 1]; grp[n_groups].cta0 = total CTAs
+    int32_t T, n_groups;
+    int32_t t0, nt;          // template range written in plane mode
     // search mode
     unsigned long long *M1;  // stage-1 max-projection, packed
     const int32_t *slot_beg; // [T + 1] CSR into the slot entries
@@ -72,13 +79,12 @@ struct PeakArgs {
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_normalise(const float2 *in, float2 *out, int64_t n, int block, cudaStream_t st);
-cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, int32_t t0, int32_t nt, int b, int pad,
-                        int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st);
-cudaError_t launch_template_fft(const double2 *taps, int32_t nt, int K, int L, const double2 *tw,
-                                float2 *bank, cudaStream_t st);
+cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, const int32_t *tlist, int32_t t0, int32_t nt, int b,
+                        int pad, int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st);
+cudaError_t launch_template_fft(const double2 *taps, const int32_t *shift, const int32_t *klen, int32_t nt, int K,
+                                int L, const double2 *tw, float2 *bank, cudaStream_t st);
 cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st);
-cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int ngroups,
-                        cudaStream_t st);
+cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
 int conv_segs_per_cta(int log2L);
 cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats,
                             cudaStream_t st);
@@ -105,6 +111,14 @@ struct jerk_plan_s {
     float *d_slots = nullptr;
     int64_t slot_cap = 0;              // floats
     int32_t *d_zt = nullptr, *d_wt = nullptr;
+    // template groups (fixed at plan creation) and their CTA prefix for the current n
+    std::vector<int32_t> order;        // processing index -> t
+    std::vector<int32_t> row_of;       // t -> processing index
+    std::vector<jerk::ConvGroup> groups;
+    int32_t *d_order = nullptr;
+    jerk::ConvGroup *d_groups = nullptr;
+    int64_t groups_n = -1;
+    int64_t conv_ctas = 0;
     int32_t *d_slot_beg = nullptr, *d_slot_h = nullptr;
     int64_t *d_slot_off = nullptr, *d_slot_len = nullptr;
     jerk::FundEntry *d_fund = nullptr;

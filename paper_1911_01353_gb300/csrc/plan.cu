@@ -111,6 +111,61 @@ int tpg_for(const jerk_plan_s *pl, int nseg, int nt) {
     return (int)std::max<int64_t>(tpg, 1);
 }
 
+// Group templates by filter half-width: sort by (m_t, t), cut into runs of
+// `tpg`, process each run in ascending t (so ties keep the lowest t).  A
+// group's tap offset is b * max(m_t) and its segment length L - 2 b max(m_t).
+void build_groups(jerk_plan_s *pl, int tpg) {
+    std::vector<int32_t> idx(pl->T);
+    for (int t = 0; t < pl->T; ++t) idx[t] = t;
+    std::stable_sort(idx.begin(), idx.end(), [pl](int x, int y) { return pl->mt[x] < pl->mt[y]; });
+    pl->order.clear();
+    pl->groups.clear();
+    for (int k0 = 0; k0 < pl->T; k0 += tpg) {
+        const int k1 = std::min(pl->T, k0 + tpg);
+        std::sort(idx.begin() + k0, idx.begin() + k1);
+        int mg = 0;
+        for (int k = k0; k < k1; ++k) mg = std::max(mg, pl->mt[idx[k]]);
+        ConvGroup g;
+        g.tb = k0;
+        g.te = k1;
+        g.bM = pl->b * mg;
+        g.V = pl->L - 2 * g.bM;
+        g.cta0 = 0;
+        g.pad = 0;
+        pl->groups.push_back(g);
+    }
+    pl->order = idx;
+    pl->row_of.assign(pl->T, 0);
+    for (int k = 0; k < pl->T; ++k) pl->row_of[pl->order[k]] = k;
+}
+
+// CTA prefix of the groups for spectra of n bins; returns the total CTAs
+int64_t group_ctas(jerk_plan_s *pl, int64_t n, std::vector<ConvGroup> *out) {
+    const int64_t bN = (int64_t)pl->b * n;
+    const int segs = conv_segs_per_cta(pl->log2L);
+    int64_t c = 0;
+    std::vector<ConvGroup> g = pl->groups;
+    for (auto &x : g) {
+        x.cta0 = (int32_t)c;
+        const int64_t nseg = (bN + x.V - 1) / x.V;
+        c += (nseg + segs - 1) / segs;
+    }
+    ConvGroup end;
+    std::memset(&end, 0, sizeof(end));
+    end.cta0 = (int32_t)c;
+    g.push_back(end);
+    if (out) *out = g;
+    return c;
+}
+
+// inverse transforms one search of n bins performs
+int64_t transforms_for(const jerk_plan_s *pl, int64_t n) {
+    const int64_t bN = (int64_t)pl->b * n;
+    int64_t s = 0;
+    for (const auto &x : pl->groups) s += (int64_t)(x.te - x.tb) * ((bN + x.V - 1) / x.V);
+    return s;
+}
+
 jerk_status validate(const jerk_params *p) {
     if (!p) return JERK_EINVAL;
     if (p->dz <= 0 || p->dw <= 0 || p->zmax < 0 || p->wmax < 0) return JERK_EINVAL;
@@ -150,6 +205,8 @@ void release(jerk_plan_s *pl) {
     for (auto &m : pl->d_M) cudaFree(m);
     cudaFree(pl->d_slots);
     cudaFree(pl->d_zt);
+    cudaFree(pl->d_order);
+    cudaFree(pl->d_groups);
     cudaFree(pl->d_wt);
     cudaFree(pl->d_slot_beg);
     cudaFree(pl->d_slot_h);
@@ -194,6 +251,9 @@ jerk_status ensure_tables(jerk_plan_s *pl, int64_t n, cudaStream_t st) {
     if (pl->n_fund)
         JCHECK(cudaMemcpyAsync(pl->d_fund, pl->h_fund.data(), sizeof(FundEntry) * pl->n_fund,
                                cudaMemcpyHostToDevice, st));
+    std::vector<ConvGroup> g;
+    pl->conv_ctas = group_ctas(pl, n, &g);
+    JCHECK(cudaMemcpyAsync(pl->d_groups, g.data(), sizeof(ConvGroup) * g.size(), cudaMemcpyHostToDevice, st));
     // host vectors are reused by later calls: make sure the copies have been consumed
     JCHECK(cudaStreamSynchronize(st));
     pl->tables_n = n;
@@ -296,12 +356,9 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     const int64_t N = params->max_bins, bN = (int64_t)pl->b * N;
     const int ns = params->n_stages;
     pl->slot_cap = build_tables(pl, N, false);
-    // largest conv grid over every spectrum length the plan accepts
-    int64_t conv_blocks = 0;
-    for (int nseg = 1; nseg <= nseg_for(pl, N); ++nseg) {
-        const int tpg = tpg_for(pl, nseg, pl->T);
-        conv_blocks = std::max<int64_t>(conv_blocks, (int64_t)nseg * ((pl->T + tpg - 1) / tpg));
-    }
+    build_groups(pl, tpg_for(pl, nseg_for(pl, N), pl->T));
+    // the conv grid only grows with n
+    const int64_t conv_blocks = group_ctas(pl, N, nullptr);
     const int64_t harm_blocks = ns > 1 ? (n_cells(bN, params->stages[1]) + 255) / 256 : 0;
     pl->stat_part_cap = 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
 
@@ -325,6 +382,8 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     for (int si = 0; si < ns; ++si) TRY(dalloc(pl, &pl->d_M[si], (size_t)n_cells(bN, params->stages[si])));
     TRY(dalloc(pl, &pl->d_slots, (size_t)pl->slot_cap));
     TRY(dalloc(pl, &pl->d_zt, (size_t)pl->T));
+    TRY(dalloc(pl, &pl->d_order, (size_t)pl->T));
+    TRY(dalloc(pl, &pl->d_groups, pl->groups.size() + 1));
     TRY(dalloc(pl, &pl->d_wt, (size_t)pl->T));
     TRY(dalloc(pl, &pl->d_slot_beg, (size_t)pl->T + 1));
     // entry / fundamental counts do not depend on n
@@ -347,6 +406,7 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     TRY(cudaMallocHost((void **)&pl->h_cand, sizeof(DevCand) * (size_t)params->max_candidates));
     TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
     TRY(cudaMemcpy(pl->d_zt, pl->zt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(pl->d_order, pl->order.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(pl->d_wt, pl->wt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(pl->d_thresh, params->thresh, sizeof(float) * JERK_MAX_STAGES, cudaMemcpyHostToDevice));
     if (e == cudaSuccess) {
@@ -389,7 +449,23 @@ jerk_status jerk_plan_info(jerk_plan pl, jerk_info *info) {
     info->max_bins = pl->prm.max_bins;
     info->slot_floats = pl->slot_cap;
     info->workspace_bytes = pl->bytes;
+    info->transforms = transforms_for(pl, pl->prm.max_bins);
+    info->n_groups = (int32_t)pl->groups.size();
+    info->reserved = 0;
     info->d_bank = pl->d_bank;
+    return JERK_OK;
+}
+
+jerk_status jerk_template_row(jerk_plan pl, int32_t t, int32_t *row, int32_t *tap_offset, int32_t *seg_valid) {
+    if (!pl || t < 0 || t >= pl->T) return JERK_EINVAL;
+    const int k = pl->row_of[t];
+    const ConvGroup *g = nullptr;
+    for (const auto &x : pl->groups)
+        if (k >= x.tb && k < x.te) g = &x;
+    if (!g) return JERK_EINVAL;
+    if (row) *row = k;
+    if (tap_offset) *tap_offset = g->bM;
+    if (seg_valid) *seg_valid = g->V;
     return JERK_OK;
 }
 
@@ -397,8 +473,8 @@ jerk_status jerk_taps(jerk_plan pl, int32_t t0, int32_t nt, void *d_out, void *s
     if (!pl || !d_out || t0 < 0 || nt < 1 || (int64_t)t0 + nt > pl->T) return JERK_EINVAL;
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
-    JCHECK(launch_taps(pl->d_zt, pl->d_wt, t0, nt, pl->b, pl->prm.pad_bins, pl->b * pl->M, pl->d_gl, pl->n_gl,
-                       (double2 *)d_out, st));
+    JCHECK(launch_taps(pl->d_zt, pl->d_wt, nullptr, t0, nt, pl->b, pl->prm.pad_bins, pl->b * pl->M, pl->d_gl,
+                       pl->n_gl, (double2 *)d_out, st));
     return JERK_OK;
 }
 
@@ -406,20 +482,40 @@ jerk_status jerk_templates(jerk_plan pl, void *stream) {
     if (!pl) return JERK_EINVAL;
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
+    // per bank row (processing order): tap offset shift and filter length of its group
+    std::vector<int32_t> shift(pl->T), klen(pl->T);
+    for (const auto &g : pl->groups)
+        for (int k = g.tb; k < g.te; ++k) {
+            shift[k] = pl->b * pl->M - g.bM;
+            klen[k] = 2 * g.bM + 1;
+        }
     // process the bank in chunks so the FP64 tap buffer stays small
     const int chunk = std::max(1, std::min(pl->T, (int)((256u << 20) / ((size_t)pl->K * sizeof(double2)))));
     double2 *taps = nullptr, *tw = nullptr;
+    int32_t *d_shift = nullptr, *d_klen = nullptr;
     JCHECK(cudaMallocAsync((void **)&taps, (size_t)chunk * pl->K * sizeof(double2), st));
     cudaError_t e = cudaMallocAsync((void **)&tw, (size_t)(pl->L / 2) * sizeof(double2), st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_shift, sizeof(int32_t) * pl->T, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&d_klen, sizeof(int32_t) * pl->T, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_shift, shift.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_klen, klen.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_twiddles64(tw, pl->L, st);
-    for (int t0 = 0; t0 < pl->T && e == cudaSuccess; t0 += chunk) {
-        const int nt = std::min(chunk, pl->T - t0);
-        e = launch_taps(pl->d_zt, pl->d_wt, t0, nt, pl->b, pl->prm.pad_bins, pl->b * pl->M, pl->d_gl, pl->n_gl,
-                        taps, st);
-        if (e == cudaSuccess) e = launch_template_fft(taps, nt, pl->K, pl->L, tw, pl->d_bank + (size_t)t0 * pl->L, st);
+    for (int k0 = 0; k0 < pl->T && e == cudaSuccess; k0 += chunk) {
+        const int nt = std::min(chunk, pl->T - k0);
+        e = launch_taps(pl->d_zt, pl->d_wt, pl->d_order + k0, 0, nt, pl->b, pl->prm.pad_bins, pl->b * pl->M,
+                        pl->d_gl, pl->n_gl, taps, st);
+        if (e == cudaSuccess)
+            e = launch_template_fft(taps, d_shift + k0, d_klen + k0, nt, pl->K, pl->L, tw,
+                                    pl->d_bank + (size_t)k0 * pl->L, st);
     }
     cudaFreeAsync(taps, st);
     if (tw) cudaFreeAsync(tw, st);
+    if (d_shift) cudaFreeAsync(d_shift, st);
+    if (d_klen) cudaFreeAsync(d_klen, st);
+    // the host vectors above must outlive the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
     JCHECK(cudaEventRecord(pl->done, st));
     pl->templates_ready = true;
@@ -445,23 +541,26 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
     cudaError_t e;
     const float2 *spec = normalised_input(pl, d_spec, n, st, &e);
     JCHECK(e);
+    {
+        const jerk_status ts = ensure_tables(pl, n, st);
+        if (ts != JERK_OK) return ts;
+    }
     ConvArgs a;
     std::memset(&a, 0, sizeof(a));
     a.spec = spec;
     a.N = n;
     a.bN = (int64_t)pl->b * n;
     a.bank = pl->d_bank;
+    a.order = pl->d_order;
+    a.grp = pl->d_groups;
+    a.n_groups = (int32_t)pl->groups.size();
     a.T = pl->T;
-    a.V = pl->V;
-    a.bM = pl->b * pl->M;
-    a.nseg = nseg_for(pl, n);
-    a.tpg = tpg_for(pl, a.nseg, nt);
     a.t0 = t0;
     a.nt = nt;
     a.plane = d_out;
     a.err = pl->d_err;
-    const int ngroups = (nt + a.tpg - 1) / a.tpg;
-    JCHECK(launch_conv(pl->log2L, 1, false, a, ngroups, st));
+    a.slot_beg = pl->d_slot_beg;
+    JCHECK(launch_conv(pl->log2L, 1, false, a, (int)pl->conv_ctas, st));
     JCHECK(cudaEventRecord(pl->done, st));
     return JERK_OK;
 }
@@ -493,11 +592,10 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     a.N = n;
     a.bN = bN;
     a.bank = pl->d_bank;
+    a.order = pl->d_order;
+    a.grp = pl->d_groups;
+    a.n_groups = (int32_t)pl->groups.size();
     a.T = pl->T;
-    a.V = pl->V;
-    a.bM = pl->b * pl->M;
-    a.nseg = nseg_for(pl, n);
-    a.tpg = tpg_for(pl, a.nseg, pl->T);
     a.t0 = 0;
     a.nt = pl->T;
     a.M1 = pl->d_M[0];
@@ -508,10 +606,8 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     a.slots = pl->d_slots;
     a.stat_part = pl->d_stat_part;
     a.err = pl->d_err;
-    const int ngroups = (pl->T + a.tpg - 1) / a.tpg;
-    const int segs = conv_segs_per_cta(pl->log2L);
-    const int64_t n1 = (int64_t)((a.nseg + segs - 1) / segs) * ngroups;
-    JCHECK(launch_conv(pl->log2L, 0, sigma, a, ngroups, st));
+    const int64_t n1 = pl->conv_ctas;
+    JCHECK(launch_conv(pl->log2L, 0, sigma, a, (int)pl->conv_ctas, st));
     JCHECK(mark(pl, 2, st));
 
     // harmonic sums for stages > 1

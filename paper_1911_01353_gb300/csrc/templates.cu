@@ -65,10 +65,11 @@ __device__ __forceinline__ int halfwidth_dev(int z, int w, int pad) {
     return (4 * abs(z) + abs(w) + 7) / 8 + pad;
 }
 
-__global__ void taps_kernel(const int32_t *__restrict__ zt, const int32_t *__restrict__ wt, int32_t t0,
-                            int b, int pad, int bM, const double2 *__restrict__ gl, double2 *__restrict__ out) {
+__global__ void taps_kernel(const int32_t *__restrict__ zt, const int32_t *__restrict__ wt,
+                            const int32_t *__restrict__ tlist, int32_t t0, int b, int pad, int bM,
+                            const double2 *__restrict__ gl, double2 *__restrict__ out) {
     extern __shared__ double2 chirp[];   // [panels * kGL]
-    const int t = t0 + blockIdx.x;
+    const int t = tlist ? tlist[blockIdx.x] : t0 + (int)blockIdx.x;
     const int K = 2 * bM + 1;
     double2 *dst = out + (int64_t)blockIdx.x * K;
     const int zi = zt[t], wi = wt[t];
@@ -133,14 +134,18 @@ __global__ void twiddle64_kernel(double2 *tw, int L) {
     }
 }
 
-// G[f] = (1/L) sum_{m<K} g[m] exp(+2 pi i f m / L): radix-2 DIT in shared memory.
-__global__ void template_fft_kernel(const double2 *__restrict__ taps, int K, int L, int log2L,
+// G[f] = (1/L) sum_{m<Kg} g[m] exp(+2 pi i f m / L): radix-2 DIT in shared
+// memory.  Row i holds taps at index d + bM (bank-wide offset); the template's
+// group uses offset bM - shift[i], i.e. g[m] = taps[i][m + shift[i]], m < klen[i].
+__global__ void template_fft_kernel(const double2 *__restrict__ taps, const int32_t *__restrict__ shift,
+                                    const int32_t *__restrict__ klen, int K, int L, int log2L,
                                     const double2 *__restrict__ tw, float2 *__restrict__ bank) {
     extern __shared__ double2 buf[];   // [L]
     const double2 *g = taps + (int64_t)blockIdx.x * K;
+    const int sh = shift[blockIdx.x], kl = klen[blockIdx.x];
     for (int m = threadIdx.x; m < L; m += blockDim.x) {
         const int r = __brev(m) >> (32 - log2L);
-        buf[r] = m < K ? g[m] : make_double2(0.0, 0.0);
+        buf[r] = m < kl ? g[m + sh] : make_double2(0.0, 0.0);
     }
     __syncthreads();
     for (int len = 2; len <= L; len <<= 1) {
@@ -163,8 +168,8 @@ __global__ void template_fft_kernel(const double2 *__restrict__ taps, int K, int
         dst[f] = make_float2((float)(buf[f].x * inv), (float)(buf[f].y * inv));
 }
 
-cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, int32_t t0, int32_t nt, int b, int pad,
-                        int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st) {
+cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, const int32_t *tlist, int32_t t0, int32_t nt, int b,
+                        int pad, int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st) {
     if (n_gl != kGL) return cudaErrorInvalidValue;
     // shared memory sized for the widest template the bank can hold (half-width M = bM/b)
     const int M = bM / b;
@@ -172,7 +177,7 @@ cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, int32_t t0, int32_
     const size_t sm = (size_t)panels_max * kGL * sizeof(double2);
     cudaError_t e = cudaFuncSetAttribute(taps_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    taps_kernel<<<nt, 256, sm, st>>>(zt, wt, t0, b, pad, bM, gl, out);
+    taps_kernel<<<nt, 256, sm, st>>>(zt, wt, tlist, t0, b, pad, bM, gl, out);
     return cudaGetLastError();
 }
 
@@ -181,15 +186,15 @@ cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_template_fft(const double2 *taps, int32_t nt, int K, int L, const double2 *tw,
-                                float2 *bank, cudaStream_t st) {
+cudaError_t launch_template_fft(const double2 *taps, const int32_t *shift, const int32_t *klen, int32_t nt, int K,
+                                int L, const double2 *tw, float2 *bank, cudaStream_t st) {
     int log2L = 0;
     while ((1 << log2L) < L) ++log2L;
     const size_t sm = (size_t)L * sizeof(double2);
     cudaError_t e =
         cudaFuncSetAttribute(template_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    template_fft_kernel<<<nt, 512, sm, st>>>(taps, K, L, log2L, tw, bank);
+    template_fft_kernel<<<nt, 512, sm, st>>>(taps, shift, klen, K, L, log2L, tw, bank);
     return cudaGetLastError();
 }
 

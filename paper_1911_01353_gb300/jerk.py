@@ -22,7 +22,7 @@ THRESH_ABS, THRESH_SIGMA = 0, 1
 EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host",
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
-           "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc")
+           "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -49,7 +49,8 @@ class Info(ctypes.Structure):
                 ("bank_halfwidth", ctypes.c_int32), ("taps", ctypes.c_int32),
                 ("seg_len", ctypes.c_int32), ("seg_valid", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("max_bins", ctypes.c_int64), ("slot_floats", ctypes.c_int64),
-                ("workspace_bytes", ctypes.c_int64), ("d_bank", ctypes.c_void_p)]
+                ("workspace_bytes", ctypes.c_int64), ("transforms", ctypes.c_int64),
+                ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32), ("d_bank", ctypes.c_void_p)]
 
 
 _lib = None
@@ -83,6 +84,7 @@ def lib() -> ctypes.CDLL:
             "jerk_profile": ([vp, i32], st),
             "jerk_phase_times": ([vp, ctypes.POINTER(ctypes.c_float), i32], st),
             "jerk_peaks_noalloc": ([vp, i64, ctypes.c_float, i32, i32, i32, i32, i32, vp, i64, vp, vp], st),
+            "jerk_template_row": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -212,6 +214,13 @@ class Plan:
         th = (ctypes.c_float * k)()
         _check(lib().jerk_stats(self._h, mu, sd, th), "jerk_stats")
         return list(mu), list(sd), list(th)
+
+    def template_row(self, t: int):
+        """(bank row, group tap offset bM_g, group segment length V_g) of template t."""
+        r, o, v = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().jerk_template_row(self._h, t, ctypes.byref(r), ctypes.byref(o), ctypes.byref(v)),
+               "jerk_template_row")
+        return r.value, o.value, v.value
 
     def profile(self, enable: bool = True):
         _check(lib().jerk_profile(self._h, 1 if enable else 0), "jerk_profile")

@@ -115,15 +115,21 @@ def test_bank_spectra(pkg):
         from paper_1911_01353_gb300.jerk import _DevArray
         bank = torch.as_tensor(_DevArray(plan.info.d_bank, T * L * 2, "<f4"), device="cuda").cpu().numpy()
         bank = bank.view(np.complex64).reshape(T, L)
+        plan_rows = {t: plan.template_row(t) for t in range(T)}
+        assert sorted(r for r, _, _ in plan_rows.values()) == list(range(T))
     ob = oracle.Bank(op)
-    bM = (K - 1) // 2
-    for t in (0, 17, 73, T - 1):
+    rows = set()
+    for t in (0, 17, 73, 100, T - 1):
+        row, bMg, Vg = plan_rows[t]
+        rows.add(row)
+        assert Vg == L - 2 * bMg and bMg >= 2 * oracle.halfwidth(int(ob.zt[t]), int(ob.wt[t]), 16)
         c = ob.taps(t)
         D = (c.size - 1) // 2
         g = np.zeros(L, complex)
-        g[bM - D: bM + D + 1] = c
+        g[bMg - D: bMg + D + 1] = c
         want = np.fft.ifft(g)          # (1/L) sum_m g[m] e^{+2 pi i f m / L}
-        assert np.max(np.abs(bank[t] - want)) < 2e-7 * np.max(np.abs(want)) + 1e-9
+        assert np.max(np.abs(bank[row] - want)) < 2e-7 * np.max(np.abs(want)) + 1e-9
+    assert len(rows) == 5
 
 
 # ---------------------------------------------------------------------------
