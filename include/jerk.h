@@ -56,6 +56,7 @@ typedef enum {
 
 enum { JERK_THRESH_ABS = 0, JERK_THRESH_SIGMA = 1 };
 enum { JERK_MAX_STAGES = 4, JERK_MAX_HARMONIC = 8 };
+enum { JERK_BATCH_GRAPH = 1 };
 
 /* Search parameters.  Sec. 2 defines the (z, w) filters; Sec. 3 the
  * user threshold, statistics and harmonic sum. */
@@ -71,8 +72,10 @@ typedef struct {
     float   thresh[4];       /* ABS: power; SIGMA: T in theta = mu + T sigma */
     int32_t norm_block;      /* B in bins (1..4096), 0 = input already normalised */
     int32_t precision;       /* 0 = FP32 (the only value accepted) */
-    int64_t max_bins;        /* capacity: largest N a search may use */
-    int64_t max_candidates;  /* capacity of the plan's candidate buffer */
+    int64_t max_bins;        /* capacity: largest N a search may use (total over a batch), <= 2^29 */
+    int64_t max_candidates;  /* capacity of the plan's candidate buffer (total over a batch) */
+    int32_t max_batch;       /* largest number of spectra in one jerk_search_batch; 0 = 1 */
+    int32_t reserved;        /* must be 0 */
 } jerk_params;
 
 /* One candidate: a peak of the stage-H max-projection over (z, w). */
@@ -84,7 +87,7 @@ typedef struct {
     int32_t stage;           /* H */
     float   z, w;            /* z_i, w_j of the fundamental */
     float   power;           /* S_H at (p, t) in normalised power units (FP32) */
-    int32_t reserved;
+    int32_t item;            /* spectrum of the batch (0 for jerk_search) */
 } jerk_candidate;
 
 /* Read-only description of a plan (sizes derived from the parameters). */
@@ -134,6 +137,21 @@ jerk_status jerk_search(jerk_plan plan, const void *d_spec, int64_t n, void *str
  * spectrum is copied into a plan-owned device buffer on `stream` first. */
 jerk_status jerk_search_host(jerk_plan plan, const void *h_spec, int64_t n, void *stream);
 
+/* Search `count` independent spectra (e.g. DM trials) of uneven lengths at
+ * once: d_specs[i] is complex64[n[i]] on the device, count <= max_batch and
+ * sum(n) <= max_bins.  Every spectrum goes through the same path as
+ * jerk_search and gives the same candidates it would give alone; the fused
+ * filter stage runs as ONE launch over all (spectrum, template group,
+ * segment) work items.  With flags & JERK_BATCH_GRAPH the sequence (copy-in,
+ * normalisation, filtering, harmonic sums, statistics, peaks) is captured into
+ * a CUDA graph the first time a set of lengths is seen and replayed after
+ * that; the caller's buffers are copied into the plan first, so they may
+ * differ between calls.  Candidates (jerk_candidates) carry the spectrum index
+ * in `item` and are sorted by (item, stage, p).  A new set of lengths
+ * rebuilds the launch tables (a host synchronisation). */
+jerk_status jerk_search_batch(jerk_plan plan, const void *const *d_specs, const int64_t *n, int32_t count,
+                              int32_t flags, void *stream);
+
 /* Wait for the last search to finish and copy its candidates to h_out
  * (capacity cap records), sorted by (stage position, p).  *n_out receives
  * the number found.  If it exceeds cap (JERK_EOVERFLOW, first cap records
@@ -179,16 +197,18 @@ jerk_status jerk_taps(jerk_plan plan, int32_t t0, int32_t nt, void *d_out, void 
 jerk_status jerk_plane(jerk_plan plan, const void *d_spec, int64_t n, int32_t t0, int32_t nt,
                        float *d_out, void *stream);
 
-/* After a search: device pointer to the stage-`stage_idx` max-projection,
- * uint64[n_cells] with n_cells = floor((b n - 1)/H) + 1, each entry
+/* After a search: device pointer to the stage-`stage_idx` max-projection of
+ * spectrum `item` (0 for jerk_search), uint64[n_cells] with
+ * n_cells = floor((b n - 1)/H) + 1, each entry
  * (float bits of M_H(p)) << 32 | (0xFFFFFFFF - t).  Valid until the next
  * search on the plan. */
-jerk_status jerk_maxproj(jerk_plan plan, int32_t stage_idx, const uint64_t **d_out, int64_t *n_cells);
+jerk_status jerk_maxproj(jerk_plan plan, int32_t item, int32_t stage_idx, const uint64_t **d_out, int64_t *n_cells);
 
-/* After a search (synchronises it): per stage mean and standard deviation
- * of S_H over its defined cells (computed only in SIGMA mode, else 0) and
- * the FP32 threshold applied.  Arrays of n_stages entries; any may be NULL. */
-jerk_status jerk_stats(jerk_plan plan, double *h_mean, double *h_std, float *h_theta);
+/* After a search (synchronises it): for spectrum `item`, per stage mean and
+ * standard deviation of S_H over its defined cells (computed only in SIGMA
+ * mode, else 0) and the FP32 threshold applied.  Arrays of n_stages entries;
+ * any may be NULL. */
+jerk_status jerk_stats(jerk_plan plan, int32_t item, double *h_mean, double *h_std, float *h_theta);
 
 /* ---- per-stage timing (the paper's run-time breakdown, Sec. 3 / Fig. 3) ---- */
 

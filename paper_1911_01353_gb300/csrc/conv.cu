@@ -132,12 +132,13 @@ __device__ __forceinline__ auto make_tw(const float2 *tab, int j) {
 
 // Store the staged power row of one template into its harmonic-row slots
 // (entries e0..e1): cells q = h p of this segment, p within the row.
-__device__ __forceinline__ void store_rows(const ConvArgs &a, const float *pw, const int (*sb)[2], int e0, int e1,
-                                           int s0, int j, int NT) {
+__device__ __forceinline__ void store_rows(const ConvArgs &a, const int64_t *soff, const int64_t *slen,
+                                           const float *pw, const int (*sb)[2], int e0, int e1, int s0, int j,
+                                           int NT) {
     for (int e = e0; e < e1; ++e) {
         const int h = __ldg(a.slot_h + e);
-        float *dst = a.slots + __ldg(a.slot_off + e);
-        const int len = (int)__ldg(a.slot_len + e);
+        float *dst = a.slots + __ldg(soff + e);
+        const int len = (int)__ldg(slen + e);
         const int pf = sb[h - 1][0];
         const int pl = min(sb[h - 1][1], len - 1);
         if (pl < pf) continue;                                // this segment is past the row's end
@@ -166,6 +167,9 @@ conv_kernel(ConvArgs a) {
     __shared__ int rel[NBUF];                                 // segments done reading a buffer
     __shared__ int issued[NBUF];                              // bulk copies issued per buffer
     __shared__ double red[2][32];
+    __shared__ double dacc[STATS ? 2 : 1][STATS ? ConvCfg<LOG2L>::THREADS : 1];   // FP64 statistics per thread
+    __shared__ float facc[STATS ? 2 : 1][STATS ? ConvCfg<LOG2L>::THREADS : 1];    // FP32 partial (32 templates)
+    __shared__ int spend[SEGS][2];                            // slot entries of the staged row
 
     const int tid = threadIdx.x;
     const int half = tid / NT;                                // which segment of the CTA
@@ -176,16 +180,23 @@ conv_kernel(ConvArgs a) {
     uint16_t *amx = reinterpret_cast<uint16_t *>(reinterpret_cast<float *>(twtab + CC::TWN) + SEGS * L) +
                     half * L;                                  // argmax per cell, as t - tb
     __shared__ int sbound[SEGS][JERK_MAX_HARMONIC][2];        // per h: first and last p of the segment
+    __shared__ const int64_t *srow[SEGS][2];                  // this segment's row offset / length tables
+    __shared__ unsigned long long *sM1[SEGS];                 // this segment's stage-1 max-projection
     const SyncNamed bar_half{1 + half, NT};
 
-    // template group of this CTA (groups are few; CTAs are group-major)
-    int g = 0;
-    while (g + 1 < a.n_groups && (int)blockIdx.x >= __ldg(&a.grp[g + 1].cta0)) ++g;
+    // (spectrum, template group) entry of this CTA: binary search of the CTA prefix
+    int lo = 0, hi = a.n_work - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)blockIdx.x >= __ldg(&a.grp[mid].cta0)) lo = mid; else hi = mid - 1;
+    }
+    const int g = lo;
+    const int item = __ldg(&a.grp[g].item);
+#define itm (a.items + item)
     const int V = __ldg(&a.grp[g].V), bM = __ldg(&a.grp[g].bM);
-    const int64_t tb = __ldg(&a.grp[g].tb), te = __ldg(&a.grp[g].te);
+    const int tb = __ldg(&a.grp[g].tb), te = __ldg(&a.grp[g].te);
     const int s = ((int)blockIdx.x - __ldg(&a.grp[g].cta0)) * SEGS + half;
-    const int64_t seg0 = (int64_t)s * V;                      // first output cell
-    const int64_t in0 = seg0 - bM;                            // first spread sample (even)
+    const int seg0 = s * V;                                   // first output cell (< 2^31: max_bins <= 2^29)
 
     if (tid < NBUF) {
         mbar_init(&full[tid], 1);
@@ -193,11 +204,17 @@ conv_kernel(ConvArgs a) {
         issued[tid] = 0;
     }
     if constexpr (CC::TWS) fill_twiddle_tables<LOG2L>(twtab, tid, CC::THREADS);
+    if (j == 0) {
+        srow[half][0] = itm->slot_off;
+        srow[half][1] = itm->slot_len;
+        sM1[half] = itm->M1;
+    }
     if (j < JERK_MAX_HARMONIC) {
         // harmonic slots: cells q = h p in [seg0, seg0 + V), q < bN
+        const int64_t bN = itm->bN;
         const int64_t h = j + 1;
         int64_t pl = (seg0 + V - 1) / h;
-        const int64_t pmax = (a.bN - 1) / h;
+        const int64_t pmax = (bN - 1) / h;
         sbound[half][j][0] = (int)((seg0 + h - 1) / h);
         sbound[half][j][1] = (int)(pl < pmax ? pl : pmax);
     }
@@ -205,18 +222,21 @@ conv_kernel(ConvArgs a) {
     if (tid == 0)
         for (int b = 0; b < NBUF && tb + b < te; ++b) {
             issued[b] = 1;
-            bulk_load(smem + b * L, a.bank + (tb + b) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+            bulk_load(smem + b * L, a.bank + (int64_t)(tb + b) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
         }
 
     // ---- 1. forward FFT of the spread segment -------------------------------
     float2 v[16];
     {
         const auto twf = make_tw<LOG2L, -1>(twtab, j);
+        const float2 *spec = itm->spec;
+        const int64_t N = itm->N;
+        const int64_t in0 = (int64_t)seg0 - bM;               // first spread sample (even)
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
             const int64_t q = in0 + j + NT * m;               // spread sample index
             float2 x = make_float2(0.f, 0.f);
-            if (((q & 1) == 0) && q >= 0 && (q >> 1) < a.N) x = a.spec[q >> 1];
+            if (((q & 1) == 0) && q >= 0 && (q >> 1) < N) x = spec[q >> 1];
             v[m] = x;
         }
         fft_pass0<LOG2L, -1>(v, twf);
@@ -237,24 +257,31 @@ conv_kernel(ConvArgs a) {
     const auto twi = make_tw<LOG2L, +1>(twtab, j);
     const int rv = fft_rev<LOG2L>(j);
     unsigned vmask = 0;
+    {
+        const int64_t bN = itm->bN;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-        const int cell = rv + NT * r;
-        if (cell < V && seg0 + cell < a.bN) vmask |= 1u << r;
+        for (int r = 0; r < 16; ++r) {
+            const int cell = rv + NT * r;
+            if (cell < V && seg0 + cell < bN) vmask |= 1u << r;
+        }
     }
+
     float mx[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) mx[r] = -1.0f;
-    double d1 = 0.0, d2 = 0.0;
-    float c1 = 0.f, c2 = 0.f;
-    int nchunk = 0;
+    if constexpr (STATS) {
+        dacc[0][tid] = 0.0;
+        dacc[1][tid] = 0.0;
+        facc[0][tid] = 0.f;
+        facc[1][tid] = 0.f;
+    }
+    if (j == 0) spend[half][0] = spend[half][1] = 0;
     // Template pipeline: template t sits in buffer b = (t - tb) % NBUF; the
     // last segment of the CTA to finish reading a buffer refills it with
     // template t + NBUF, so the segments never wait on each other.
     bool failed = false;
-    int pend0 = 0, pend1 = 0;                                 // slot entries of the staged row
-    for (int64_t k = tb; k < te; ++k) {                     // processing index
-        const int it = (int)(k - tb);
+    for (int k = tb; k < te; ++k) {                         // processing index
+        const int it = k - tb;
         const int t = __ldg(a.order + k);                     // template index
         const int b = it % NBUF;
         const float2 *tsm = smem + b * L;
@@ -273,12 +300,14 @@ conv_kernel(ConvArgs a) {
             rel[b] = 0;
             if (k + NBUF < te) {
                 issued[b] += 1;
-                bulk_load(smem + b * L, a.bank + (k + NBUF) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+                bulk_load(smem + b * L, a.bank + (int64_t)(k + NBUF) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
             }
         }
         fft_store0<LOG2L>(v, work, j);
         if constexpr (MODE == 0)
-            if (pend0 < pend1) store_rows(a, stage, sbound[half], pend0, pend1, (int)seg0, j, NT);
+            if (spend[half][0] < spend[half][1])
+                store_rows(a, srow[half][0], srow[half][1], stage, sbound[half], spend[half][0], spend[half][1],
+                           (int)seg0, j, NT);
         fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
 #pragma unroll
@@ -293,20 +322,24 @@ conv_kernel(ConvArgs a) {
                 }
             }
             if constexpr (STATS) {
-                float q[16], q2[16];
+                // invalid cells (overlap, beyond the spectrum) count as 0; the staged
+                // row is never read back at those cells
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
-                    q[r] = (vmask >> r) & 1u ? P[r] : 0.f;
-                    q2[r] = q[r] * q[r];
-                }
-                c1 += tree16(q);
-                c2 += tree16(q2);
-                if (++nchunk == 32) {
-                    d1 += (double)c1;
-                    d2 += (double)c2;
+                for (int r = 0; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                float c1 = facc[0][tid] + tree16(P);
+                float sq[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) sq[i] = fmaf(P[2 * i], P[2 * i], P[2 * i + 1] * P[2 * i + 1]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sq[i] = sq[2 * i] + sq[2 * i + 1];
+                float c2 = facc[1][tid] + ((sq[0] + sq[1]) + (sq[2] + sq[3]));
+                if ((it & 31) == 31) {
+                    dacc[0][tid] += (double)c1;
+                    dacc[1][tid] += (double)c2;
                     c1 = c2 = 0.f;
-                    nchunk = 0;
                 }
+                facc[0][tid] = c1;
+                facc[1][tid] = c2;
             }
             // harmonic rows of this template: stage the power row now, store it
             // during the next template's transform (whose barriers order it)
@@ -315,10 +348,12 @@ conv_kernel(ConvArgs a) {
 #pragma unroll
                 for (int r = 0; r < 16; ++r) stage[swzf(rv + NT * r)] = P[r];
             }
-            pend0 = e0;
-            pend1 = e1;
+            if (j == 0) {
+                spend[half][0] = e0;
+                spend[half][1] = e1;
+            }
         } else if (t >= a.t0 && t < a.t0 + a.nt) {
-            float *row = a.plane + (int64_t)(t - a.t0) * a.bN + seg0;
+            float *row = a.plane + (int64_t)(t - a.t0) * (2 * (int64_t)a.items[0].N) + seg0;
 #pragma unroll
             for (int r = 0; r < 16; ++r)
                 if ((vmask >> r) & 1u) row[rv + NT * r] = P[r];
@@ -326,10 +361,10 @@ conv_kernel(ConvArgs a) {
     }
 
     if constexpr (MODE == 0) {
-        if (!failed && pend0 < pend1) {
-            bar_half();
-            store_rows(a, stage, sbound[half], pend0, pend1, (int)seg0, j, NT);
-        }
+        bar_half();
+        if (!failed && spend[half][0] < spend[half][1])
+            store_rows(a, srow[half][0], srow[half][1], stage, sbound[half], spend[half][0], spend[half][1],
+                       (int)seg0, j, NT);
     }
     __syncthreads();
     if (tid == 0) {
@@ -344,12 +379,12 @@ conv_kernel(ConvArgs a) {
                 const unsigned long long packed =
                     ((unsigned long long)__float_as_uint(mx[r]) << 32) |
                     (unsigned long long)(0xFFFFFFFFu - (unsigned)__ldg(a.order + tb + amx[rv + NT * r]));
-                atomicMax(a.M1 + seg0 + rv + NT * r, packed);
+                atomicMax(sM1[half] + seg0 + rv + NT * r, packed);
             }
         }
         if constexpr (STATS) {
-            d1 += (double)c1;
-            d2 += (double)c2;
+            double d1 = dacc[0][tid] + (double)facc[0][tid];
+            double d2 = dacc[1][tid] + (double)facc[1][tid];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 d1 += __shfl_xor_sync(0xffffffffu, d1, o);
@@ -373,6 +408,8 @@ conv_kernel(ConvArgs a) {
         }
     }
 }
+
+#undef itm
 
 int conv_segs_per_cta(int log2L) { return log2L >= 13 ? 1 : 2; }
 

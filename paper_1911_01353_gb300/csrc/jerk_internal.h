@@ -16,7 +16,7 @@ struct DevCand {
     int32_t t;
     int32_t stage_idx;
     float power;
-    int32_t pad;
+    int32_t item;            // spectrum of the batch
 };
 
 // A fundamental template with its harmonic-row slots (h = 1 .. h_top).
@@ -28,26 +28,32 @@ struct FundEntry {
 
 // A group of templates processed together: templates with similar half-width
 // share a tap offset bM and segment length V (processing indices tb..te-1 of
-// the bank); cta0 is the group's first CTA in the launch.
+// the bank).  In a launch table, cta0 is the entry's first CTA and item the
+// spectrum it works on.
 struct ConvGroup {
-    int32_t tb, te, V, bM, cta0, pad;
+    int32_t tb, te, V, bM, cta0, item;
+};
+
+// One spectrum of a launch (a batch of independent spectra, or just one).
+struct ItemDesc {
+    const float2 *spec;      // normalised spectrum, N bins
+    int64_t N, bN;
+    unsigned long long *M1;  // stage-1 max-projection of this spectrum
+    const int64_t *slot_off; // [n_entries] harmonic-row offsets of this spectrum (floats)
+    const int64_t *slot_len; // [n_entries] harmonic-row lengths
 };
 
 // Arguments of the fused overlap-and-save kernel.
 struct ConvArgs {
-    const float2 *spec;      // normalised spectrum, N bins
-    int64_t N, bN;
+    const ItemDesc *items;   // spectra of the launch
     const float2 *bank;      // [T][L] template spectra in processing order
     const int32_t *order;    // processing index -> template index t
-    const ConvGroup *grp;    // [n_groups + 1]; grp[n_groups].cta0 = total CTAs
-    int32_t T, n_groups;
+    const ConvGroup *grp;    // [n_work + 1] (item, group) entries; grp[n_work].cta0 = total CTAs
+    int32_t T, n_work;
     int32_t t0, nt;          // template range written in plane mode
     // search mode
-    unsigned long long *M1;  // stage-1 max-projection, packed
     const int32_t *slot_beg; // [T + 1] CSR into the slot entries
     const int32_t *slot_h;
-    const int64_t *slot_off;
-    const int64_t *slot_len;
     float *slots;
     double *stat_part;       // [gridDim.y][gridDim.x][2]
     int *err;                // set to 1 when a bounded device wait expires
@@ -72,6 +78,7 @@ struct PeakArgs {
     int64_t n_cells[JERK_MAX_STAGES];
     const float *theta;                    // device, per stage
     int32_t n_stages;
+    int32_t item;
     DevCand *out;
     int64_t cap;
     unsigned long long *count;
@@ -98,6 +105,24 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 
 }  // namespace jerk
 
+// Launch tables of one set of spectrum lengths (a batch, or one spectrum).
+struct BatchLayout {
+    std::vector<int64_t> n;                        // lengths: the cache key
+    int64_t total_ctas = 0;
+    int n_work = 0;
+    std::vector<int64_t> item_cta0;                // [count + 1] conv CTAs of each item
+    std::vector<int64_t> harm0;                    // [count + 1] harmonic partial blocks of each item
+    std::vector<int64_t> spec_off;                 // [count] offset in the normalised-spectrum buffer
+    std::vector<int64_t> m_off[JERK_MAX_STAGES];   // [count] offset in each max-projection buffer
+    std::vector<int64_t> slot_base;                // [count + 1] harmonic-row floats of each item
+    jerk::ItemDesc *d_items = nullptr;
+    jerk::ConvGroup *d_work = nullptr;
+    int64_t *d_soff = nullptr, *d_slen = nullptr;  // [count][n_entries]
+    jerk::FundEntry *d_fund = nullptr;             // [count][n_fund]
+    double *d_counts = nullptr;                    // [count][JERK_MAX_STAGES]
+    cudaGraphExec_t graph = nullptr;               // captured batch sequence
+};
+
 struct jerk_plan_s {
     jerk_params prm;
     int device;
@@ -116,13 +141,16 @@ struct jerk_plan_s {
     std::vector<int32_t> row_of;       // t -> processing index
     std::vector<jerk::ConvGroup> groups;
     int32_t *d_order = nullptr;
-    jerk::ConvGroup *d_groups = nullptr;
-    int64_t groups_n = -1;
-    int64_t conv_ctas = 0;
+
     int32_t *d_slot_beg = nullptr, *d_slot_h = nullptr;
-    int64_t *d_slot_off = nullptr, *d_slot_len = nullptr;
-    jerk::FundEntry *d_fund = nullptr;
     int n_entries = 0, n_fund = 0;
+    // harmonic-row structure (independent of n): entry e of the CSR (by
+    // producing template) is harmonic ent_h[e] of fundamental ent_f[e]
+    std::vector<int32_t> ent_f, ent_h, fund_t, fund_top;
+    std::vector<int32_t> fh_entry;     // [n_fund][JERK_MAX_HARMONIC] -> entry (or -1)
+    int32_t max_batch = 1;
+    BatchLayout lay;                   // tables of the last set of lengths
+    cudaStream_t cap_stream = nullptr; // private stream graphs are captured on
     double *d_stat_part = nullptr;     // conv partials then harmonic partials
     int64_t stat_part_cap = 0;         // doubles
     double *d_stats = nullptr;         // [n_stages][2]
@@ -135,14 +163,10 @@ struct jerk_plan_s {
     double2 *d_gl = nullptr;
     int n_gl = 0;
     int64_t bytes = 0;
-    // host-side slot tables for the current n
     std::vector<int32_t> h_slot_beg, h_slot_h;
-    std::vector<int64_t> h_slot_off, h_slot_len;
-    std::vector<jerk::FundEntry> h_fund;
-    int64_t tables_n = -1;
     // state
     bool templates_ready = false;
-    int64_t last_n = 0;
+    int32_t last_count = 0;            // spectra of the last search
     bool searched = false;
     cudaEvent_t done = nullptr;
     bool profile = false, profiled = false;

@@ -294,7 +294,7 @@ __global__ void peaks_kernel(PeakArgs a) {
                 c.t = (int32_t)(0xFFFFFFFFu - (unsigned)(x & 0xFFFFFFFFull));
                 c.stage_idx = si;
                 c.power = v;
-                c.pad = 0;
+                c.item = a.item;
                 a.out[idx] = c;
             }
         }

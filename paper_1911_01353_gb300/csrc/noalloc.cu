@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) write_kernel(const unsigned long lon
         rec.z = (float)(-g.zmax + rec.z_idx * g.dz);
         rec.w = (float)(-g.wmax + rec.w_idx * g.dw);
         rec.power = mval(x);
-        rec.reserved = 0;
+        rec.item = 0;
         out[k] = rec;
     }
 }

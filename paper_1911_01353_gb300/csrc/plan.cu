@@ -1,5 +1,7 @@
 // Host side of libjerk.so: parameter validation, plan sizing, the template
-// bank, the launch sequence of a search and the candidate read-back.
+// bank, the launch sequence of a search (one spectrum or a batch of
+// independent spectra, optionally replayed from a CUDA graph) and the
+// candidate read-back.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -22,9 +24,9 @@ jerk_status from_cuda(cudaError_t e) {
     return JERK_ECUDA;
 }
 
-#define JCHECK(x)                                  \
-    do {                                           \
-        cudaError_t e_ = (x);                      \
+#define JCHECK(x)                                    \
+    do {                                             \
+        cudaError_t e_ = (x);                        \
         if (e_ != cudaSuccess) return from_cuda(e_); \
     } while (0)
 
@@ -45,56 +47,72 @@ int index_of(const jerk_plan_s *pl, int z, int w) {
     return j * pl->nz + i;
 }
 
-// Slot tables for spectra of n bins: for every harmonic h of every
-// fundamental valid at the smallest stage >= max(h, 2), one float row of
-// n_cells(bN, that stage) entries indexed by the fundamental cell p.
-int64_t build_tables(jerk_plan_s *pl, int64_t n, bool fill) {
-    const int64_t bN = (int64_t)pl->b * n;
+int64_t round32(int64_t x) { return (x + 31) / 32 * 32; }
+
+// Harmonic-row structure (independent of the spectrum length): for every
+// harmonic h of every fundamental valid at the smallest stage >= max(h, 2),
+// one row written by template (h z, h w); entries in CSR order by that template.
+void build_row_structure(jerk_plan_s *pl) {
     const int ns = pl->prm.n_stages;
-    struct Ent { int32_t t, h; int64_t off, len; };
+    struct Ent { int32_t t, f, h; };
     std::vector<Ent> ents;
-    std::vector<FundEntry> fund;
-    int64_t off = 0;
+    pl->fund_t.clear();
+    pl->fund_top.clear();
     if (ns > 1) {
         for (int t = 0; t < pl->T; ++t) {
             int top = 0;
             for (int si = 1; si < ns; ++si)
                 if (valid_at(pl, t, pl->prm.stages[si])) top = si;
             if (top == 0) continue;
-            FundEntry fe;
-            std::memset(&fe, 0, sizeof(fe));
-            fe.t = t;
-            fe.top_stage = top;
-            const int Htop = pl->prm.stages[top];
-            for (int h = 1; h <= Htop; ++h) {
-                int sn = 1;
-                while (pl->prm.stages[sn] < std::max(h, 2)) ++sn;
-                const int64_t len = n_cells(bN, pl->prm.stages[sn]);
-                fe.off[h - 1] = off;
-                if (fill) ents.push_back({index_of(pl, h * pl->zt[t], h * pl->wt[t]), h, off, len});
-                off += (len + 31) / 32 * 32;   // 128-byte aligned rows (16-byte loads, padded tail)
-            }
-            if (fill) fund.push_back(fe);
+            const int f = (int)pl->fund_t.size();
+            pl->fund_t.push_back(t);
+            pl->fund_top.push_back(top);
+            for (int h = 1; h <= pl->prm.stages[top]; ++h)
+                ents.push_back({index_of(pl, h * pl->zt[t], h * pl->wt[t]), f, h});
         }
     }
-    if (fill) {
-        std::stable_sort(ents.begin(), ents.end(), [](const Ent &x, const Ent &y) { return x.t < y.t; });
-        pl->h_slot_beg.assign(pl->T + 1, 0);
-        pl->h_slot_h.resize(ents.size());
-        pl->h_slot_off.resize(ents.size());
-        pl->h_slot_len.resize(ents.size());
-        for (size_t e = 0; e < ents.size(); ++e) {
-            pl->h_slot_beg[ents[e].t + 1]++;
-            pl->h_slot_h[e] = ents[e].h;
-            pl->h_slot_off[e] = ents[e].off;
-            pl->h_slot_len[e] = ents[e].len;
-        }
-        for (int t = 0; t < pl->T; ++t) pl->h_slot_beg[t + 1] += pl->h_slot_beg[t];
-        pl->h_fund = fund;
-        pl->n_entries = (int)ents.size();
-        pl->n_fund = (int)fund.size();
+    std::stable_sort(ents.begin(), ents.end(), [](const Ent &x, const Ent &y) { return x.t < y.t; });
+    pl->n_entries = (int)ents.size();
+    pl->n_fund = (int)pl->fund_t.size();
+    pl->h_slot_beg.assign(pl->T + 1, 0);
+    pl->h_slot_h.resize(ents.size());
+    pl->ent_f.resize(ents.size());
+    pl->ent_h.resize(ents.size());
+    pl->fh_entry.assign((size_t)pl->n_fund * JERK_MAX_HARMONIC, -1);
+    for (size_t e = 0; e < ents.size(); ++e) {
+        pl->h_slot_beg[ents[e].t + 1]++;
+        pl->h_slot_h[e] = ents[e].h;
+        pl->ent_f[e] = ents[e].f;
+        pl->ent_h[e] = ents[e].h;
+        pl->fh_entry[(size_t)ents[e].f * JERK_MAX_HARMONIC + ents[e].h - 1] = (int32_t)e;
     }
-    return off;
+    for (int t = 0; t < pl->T; ++t) pl->h_slot_beg[t + 1] += pl->h_slot_beg[t];
+}
+
+// Row offsets and lengths of one spectrum of n bins whose rows start at
+// `base` (floats); returns the floats used.  Rows are 128-byte aligned.
+int64_t item_rows(const jerk_plan_s *pl, int64_t n, int64_t base, int64_t *soff, int64_t *slen, FundEntry *fund) {
+    const int64_t bN = (int64_t)pl->b * n;
+    int64_t off = base;
+    for (int f = 0; f < pl->n_fund; ++f) {
+        FundEntry fe;
+        std::memset(&fe, 0, sizeof(fe));
+        fe.t = pl->fund_t[f];
+        fe.top_stage = pl->fund_top[f];
+        const int Htop = pl->prm.stages[fe.top_stage];
+        for (int h = 1; h <= Htop; ++h) {
+            int sn = 1;
+            while (pl->prm.stages[sn] < std::max(h, 2)) ++sn;
+            const int64_t len = n_cells(bN, pl->prm.stages[sn]);
+            fe.off[h - 1] = off;
+            const int e = pl->fh_entry[(size_t)f * JERK_MAX_HARMONIC + h - 1];
+            if (soff) soff[e] = off;
+            if (slen) slen[e] = len;
+            off += round32(len);
+        }
+        if (fund) fund[f] = fe;
+    }
+    return off - base;
 }
 
 int nseg_for(const jerk_plan_s *pl, int64_t n) {
@@ -131,7 +149,7 @@ void build_groups(jerk_plan_s *pl, int tpg) {
         g.bM = pl->b * mg;
         g.V = pl->L - 2 * g.bM;
         g.cta0 = 0;
-        g.pad = 0;
+        g.item = 0;
         pl->groups.push_back(g);
     }
     pl->order = idx;
@@ -139,22 +157,12 @@ void build_groups(jerk_plan_s *pl, int tpg) {
     for (int k = 0; k < pl->T; ++k) pl->row_of[pl->order[k]] = k;
 }
 
-// CTA prefix of the groups for spectra of n bins; returns the total CTAs
-int64_t group_ctas(jerk_plan_s *pl, int64_t n, std::vector<ConvGroup> *out) {
+// conv CTAs one spectrum of n bins needs
+int64_t ctas_for(const jerk_plan_s *pl, int64_t n) {
     const int64_t bN = (int64_t)pl->b * n;
     const int segs = conv_segs_per_cta(pl->log2L);
     int64_t c = 0;
-    std::vector<ConvGroup> g = pl->groups;
-    for (auto &x : g) {
-        x.cta0 = (int32_t)c;
-        const int64_t nseg = (bN + x.V - 1) / x.V;
-        c += (nseg + segs - 1) / segs;
-    }
-    ConvGroup end;
-    std::memset(&end, 0, sizeof(end));
-    end.cta0 = (int32_t)c;
-    g.push_back(end);
-    if (out) *out = g;
+    for (const auto &x : pl->groups) c += ((bN + x.V - 1) / x.V + segs - 1) / segs;
     return c;
 }
 
@@ -164,6 +172,12 @@ int64_t transforms_for(const jerk_plan_s *pl, int64_t n) {
     int64_t s = 0;
     for (const auto &x : pl->groups) s += (int64_t)(x.te - x.tb) * ((bN + x.V - 1) / x.V);
     return s;
+}
+
+int64_t harm_blocks_for(const jerk_plan_s *pl, int64_t n) {
+    if (pl->prm.n_stages < 2) return 0;
+    const int64_t nthreads = (n_cells((int64_t)pl->b * n, pl->prm.stages[1]) + 3) / 4;
+    return (nthreads + 255) / 256;
 }
 
 jerk_status validate(const jerk_params *p) {
@@ -182,8 +196,9 @@ jerk_status validate(const jerk_params *p) {
         if (!std::isfinite(p->thresh[i])) return JERK_EINVAL;
     if (p->norm_block < 0 || p->norm_block > 4096) return JERK_EINVAL;
     if (p->precision != 0) return JERK_EINVAL;
-    if (p->max_bins < 1 || p->max_bins > ((int64_t)1 << 30)) return JERK_EINVAL;
+    if (p->max_bins < 1 || p->max_bins > ((int64_t)1 << 29)) return JERK_EINVAL;
     if (p->max_candidates < 1 || p->max_candidates > ((int64_t)1 << 26)) return JERK_EINVAL;
+    if (p->max_batch < 0 || p->max_batch > 4096) return JERK_EINVAL;
     if (p->seg_len != 0 && (p->seg_len < 1024 || p->seg_len > 8192 || (p->seg_len & (p->seg_len - 1))))
         return JERK_EINVAL;
     return JERK_OK;
@@ -198,7 +213,19 @@ cudaError_t dalloc(jerk_plan_s *pl, T **ptr, size_t count) {
     return e;
 }
 
+void free_layout(BatchLayout &L) {
+    if (L.graph) cudaGraphExecDestroy(L.graph);
+    cudaFree(L.d_items);
+    cudaFree(L.d_work);
+    cudaFree(L.d_soff);
+    cudaFree(L.d_slen);
+    cudaFree(L.d_fund);
+    cudaFree(L.d_counts);
+    L = BatchLayout();
+}
+
 void release(jerk_plan_s *pl) {
+    free_layout(pl->lay);
     cudaFree(pl->d_bank);
     cudaFree(pl->d_spec_in);
     cudaFree(pl->d_spec_norm);
@@ -206,16 +233,11 @@ void release(jerk_plan_s *pl) {
     cudaFree(pl->d_slots);
     cudaFree(pl->d_zt);
     cudaFree(pl->d_order);
-    cudaFree(pl->d_groups);
     cudaFree(pl->d_wt);
     cudaFree(pl->d_slot_beg);
     cudaFree(pl->d_slot_h);
-    cudaFree(pl->d_slot_off);
-    cudaFree(pl->d_slot_len);
-    cudaFree(pl->d_fund);
     cudaFree(pl->d_stat_part);
     cudaFree(pl->d_stats);
-    cudaFree(pl->d_counts);
     cudaFree(pl->d_thresh);
     cudaFree(pl->d_theta);
     cudaFree(pl->d_cand);
@@ -226,47 +248,210 @@ void release(jerk_plan_s *pl) {
     if (pl->done) cudaEventDestroy(pl->done);
     for (auto &e : pl->ev)
         if (e) cudaEventDestroy(e);
+    if (pl->cap_stream) cudaStreamDestroy(pl->cap_stream);
 }
 
 // phase marker i of a profiled search
-cudaError_t mark(jerk_plan_s *pl, int i, cudaStream_t st) {
-    return pl->profile ? cudaEventRecord(pl->ev[i], st) : cudaSuccess;
+cudaError_t mark(jerk_plan_s *pl, int i, cudaStream_t st, bool capturing) {
+    return (pl->profile && !capturing) ? cudaEventRecord(pl->ev[i], st) : cudaSuccess;
 }
 
-// upload the slot tables for spectra of n bins (synchronous w.r.t. the host buffers)
-jerk_status ensure_tables(jerk_plan_s *pl, int64_t n, cudaStream_t st) {
-    if (pl->tables_n == n) return JERK_OK;
-    const int64_t need = build_tables(pl, n, true);
-    if (need > pl->slot_cap) return JERK_ENOMEM;
-    JCHECK(cudaMemcpyAsync(pl->d_slot_beg, pl->h_slot_beg.data(), sizeof(int32_t) * (pl->T + 1),
-                           cudaMemcpyHostToDevice, st));
-    if (pl->n_entries) {
-        JCHECK(cudaMemcpyAsync(pl->d_slot_h, pl->h_slot_h.data(), sizeof(int32_t) * pl->n_entries,
-                               cudaMemcpyHostToDevice, st));
-        JCHECK(cudaMemcpyAsync(pl->d_slot_off, pl->h_slot_off.data(), sizeof(int64_t) * pl->n_entries,
-                               cudaMemcpyHostToDevice, st));
-        JCHECK(cudaMemcpyAsync(pl->d_slot_len, pl->h_slot_len.data(), sizeof(int64_t) * pl->n_entries,
-                               cudaMemcpyHostToDevice, st));
-    }
-    if (pl->n_fund)
-        JCHECK(cudaMemcpyAsync(pl->d_fund, pl->h_fund.data(), sizeof(FundEntry) * pl->n_fund,
-                               cudaMemcpyHostToDevice, st));
-    std::vector<ConvGroup> g;
-    pl->conv_ctas = group_ctas(pl, n, &g);
-    JCHECK(cudaMemcpyAsync(pl->d_groups, g.data(), sizeof(ConvGroup) * g.size(), cudaMemcpyHostToDevice, st));
-    // host vectors are reused by later calls: make sure the copies have been consumed
+// Launch tables for a set of spectrum lengths (rebuilt when the set changes;
+// the host-to-device copies are synchronous).
+jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaStream_t st) {
+    if (pl->lay.n == n && pl->lay.d_items) return JERK_OK;
     JCHECK(cudaStreamSynchronize(st));
-    pl->tables_n = n;
+    free_layout(pl->lay);
+    BatchLayout &L = pl->lay;
+    const int count = (int)n.size();
+    const int ns = pl->prm.n_stages;
+    L.n = n;
+    L.item_cta0.assign(count + 1, 0);
+    L.harm0.assign(count + 1, 0);
+    L.spec_off.assign(count, 0);
+    L.slot_base.assign(count + 1, 0);
+    for (int si = 0; si < ns; ++si) L.m_off[si].assign(count, 0);
+    std::vector<int64_t> soff((size_t)count * std::max(pl->n_entries, 1)), slen(soff.size());
+    std::vector<FundEntry> fund((size_t)count * std::max(pl->n_fund, 1));
+    std::vector<ConvGroup> work;
+    std::vector<double> counts((size_t)count * JERK_MAX_STAGES, 0.0);
+    int64_t spec = 0, m[JERK_MAX_STAGES] = {0, 0, 0, 0};
+    const int segs = conv_segs_per_cta(pl->log2L);
+    for (int i = 0; i < count; ++i) {
+        const int64_t bN = (int64_t)pl->b * n[i];
+        L.spec_off[i] = spec;
+        spec += n[i];
+        for (int si = 0; si < ns; ++si) {
+            L.m_off[si][i] = m[si];
+            m[si] += n_cells(bN, pl->prm.stages[si]);
+        }
+        const int64_t used = item_rows(pl, n[i], L.slot_base[i], soff.data() + (size_t)i * pl->n_entries,
+                                       slen.data() + (size_t)i * pl->n_entries,
+                                       fund.data() + (size_t)i * pl->n_fund);
+        L.slot_base[i + 1] = L.slot_base[i] + used;
+        // conv work: this spectrum's (group, segment range) entries, item-major
+        for (const auto &g : pl->groups) {
+            ConvGroup w = g;
+            w.cta0 = (int32_t)L.total_ctas;
+            w.item = i;
+            work.push_back(w);
+            L.total_ctas += ((bN + g.V - 1) / g.V + segs - 1) / segs;
+        }
+        L.item_cta0[i + 1] = L.total_ctas;
+        L.harm0[i + 1] = L.harm0[i] + harm_blocks_for(pl, n[i]);
+        counts[(size_t)i * JERK_MAX_STAGES] = (double)bN * pl->T;
+        for (int si = 1; si < ns; ++si) {
+            int64_t nf = 0;
+            for (int f = 0; f < pl->n_fund; ++f)
+                if (pl->fund_top[f] >= si) ++nf;
+            counts[(size_t)i * JERK_MAX_STAGES + si] = (double)nf * n_cells(bN, pl->prm.stages[si]);
+        }
+    }
+    ConvGroup end;
+    std::memset(&end, 0, sizeof(end));
+    end.cta0 = (int32_t)L.total_ctas;
+    work.push_back(end);
+    L.n_work = (int)work.size() - 1;
+    // capacity checks (the plan was sized for max_bins bins in total)
+    if (spec > pl->prm.max_bins || L.slot_base[count] > pl->slot_cap ||
+        2 * (L.total_ctas + (int64_t)ns * L.harm0[count]) > pl->stat_part_cap) {
+        free_layout(pl->lay);
+        return JERK_ENOMEM;
+    }
+    for (int si = 0; si < ns; ++si)
+        if (m[si] > n_cells((int64_t)pl->b * pl->prm.max_bins, pl->prm.stages[si]) + pl->max_batch) {
+            free_layout(pl->lay);
+            return JERK_ENOMEM;
+        }
+    std::vector<ItemDesc> items(count);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_items, sizeof(ItemDesc) * count);
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_work, sizeof(ConvGroup) * work.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_soff, sizeof(int64_t) * soff.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_slen, sizeof(int64_t) * slen.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_fund, sizeof(FundEntry) * fund.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_counts, sizeof(double) * counts.size());
+    if (e != cudaSuccess) {
+        free_layout(pl->lay);
+        return from_cuda(e);
+    }
+    for (int i = 0; i < count; ++i) {
+        items[i].spec = pl->d_spec_norm + L.spec_off[i];
+        items[i].N = n[i];
+        items[i].bN = (int64_t)pl->b * n[i];
+        items[i].M1 = pl->d_M[0] + L.m_off[0][i];
+        items[i].slot_off = L.d_soff + (size_t)i * pl->n_entries;
+        items[i].slot_len = L.d_slen + (size_t)i * pl->n_entries;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(L.d_items, items.data(), sizeof(ItemDesc) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L.d_work, work.data(), sizeof(ConvGroup) * work.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.d_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(L.d_slen, slen.data(), sizeof(int64_t) * slen.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L.d_fund, fund.data(), sizeof(FundEntry) * fund.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(L.d_counts, counts.data(), sizeof(double) * counts.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_layout(pl->lay);
+        return from_cuda(e);
+    }
     return JERK_OK;
 }
 
-const float2 *normalised_input(jerk_plan_s *pl, const void *d_spec, int64_t n, cudaStream_t st, cudaError_t *err) {
-    *err = cudaSuccess;
-    if (pl->prm.norm_block > 0) {
-        *err = launch_normalise((const float2 *)d_spec, pl->d_spec_norm, n, pl->prm.norm_block, st);
-        return pl->d_spec_norm;
+// Enqueue the whole path for the spectra of the current layout.  in[i] is
+// spectrum i (device).  Capturable into a CUDA graph (no host copies, no
+// host synchronisation, no event waits).
+jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_t st, bool capturing) {
+    const BatchLayout &L = pl->lay;
+    const int count = (int)L.n.size();
+    const int ns = pl->prm.n_stages;
+    const bool sigma = pl->prm.thresh_mode == JERK_THRESH_SIGMA;
+
+    JCHECK(mark(pl, 0, st, capturing));
+    for (int i = 0; i < count; ++i) {
+        float2 *dst = pl->d_spec_norm + L.spec_off[i];
+        if (pl->prm.norm_block > 0)
+            JCHECK(launch_normalise(in[i], dst, L.n[i], pl->prm.norm_block, st));
+        else if (in[i] != dst)
+            JCHECK(cudaMemcpyAsync(dst, in[i], sizeof(float2) * L.n[i], cudaMemcpyDeviceToDevice, st));
     }
-    return (const float2 *)d_spec;
+    for (int si = 0; si < ns; ++si) {
+        const int64_t used = L.m_off[si][count - 1] + n_cells((int64_t)pl->b * L.n[count - 1], pl->prm.stages[si]);
+        JCHECK(cudaMemsetAsync(pl->d_M[si], 0, sizeof(unsigned long long) * used, st));
+    }
+    JCHECK(mark(pl, 1, st, capturing));
+
+    // fused overlap-and-save + stage-1 max-projection + harmonic rows, all spectra in one launch
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.items = L.d_items;
+    a.bank = pl->d_bank;
+    a.order = pl->d_order;
+    a.grp = L.d_work;
+    a.n_work = L.n_work;
+    a.T = pl->T;
+    a.t0 = 0;
+    a.nt = pl->T;
+    a.slot_beg = pl->d_slot_beg;
+    a.slot_h = pl->d_slot_h;
+    a.slots = pl->d_slots;
+    a.stat_part = pl->d_stat_part;
+    a.err = pl->d_err;
+    JCHECK(launch_conv(pl->log2L, 0, sigma, a, (int)L.total_ctas, st));
+    JCHECK(mark(pl, 2, st, capturing));
+
+    // harmonic sums for stages > 1, per spectrum
+    double *partH = pl->d_stat_part + 2 * L.total_ctas;
+    if (ns > 1) {
+        for (int i = 0; i < count; ++i) {
+            const int64_t bN = (int64_t)pl->b * L.n[i];
+            HarmArgs h;
+            std::memset(&h, 0, sizeof(h));
+            h.slots = pl->d_slots;
+            h.fund = L.d_fund + (size_t)i * pl->n_fund;
+            h.n_fund = pl->n_fund;
+            h.n_stages = ns;
+            for (int si = 0; si < ns; ++si) {
+                h.stages[si] = pl->prm.stages[si];
+                h.n_cells[si] = n_cells(bN, pl->prm.stages[si]);
+                h.M[si] = pl->d_M[si] + L.m_off[si][i];
+            }
+            h.stat_part = partH + 2 * ns * L.harm0[i];
+            h.f_chunk = pl->n_fund;
+            const int64_t nthreads = (h.n_cells[1] + 3) / 4;   // 4 cells per thread
+            JCHECK(launch_harmonic(h, nthreads, 1, sigma, st));
+        }
+    }
+    JCHECK(mark(pl, 3, st, capturing));
+    for (int i = 0; i < count; ++i)
+        JCHECK(launch_finalise_stats(pl->d_stat_part + 2 * L.item_cta0[i], L.item_cta0[i + 1] - L.item_cta0[i],
+                                     partH + 2 * ns * L.harm0[i], L.harm0[i + 1] - L.harm0[i], ns,
+                                     L.d_counts + (size_t)i * JERK_MAX_STAGES, pl->d_thresh, pl->prm.thresh_mode,
+                                     pl->d_stats + (size_t)i * 2 * JERK_MAX_STAGES,
+                                     pl->d_theta + (size_t)i * JERK_MAX_STAGES, st));
+
+    // peaks
+    JCHECK(mark(pl, 4, st, capturing));
+    JCHECK(cudaMemsetAsync(pl->d_count, 0, sizeof(unsigned long long), st));
+    for (int i = 0; i < count; ++i) {
+        const int64_t bN = (int64_t)pl->b * L.n[i];
+        PeakArgs pk;
+        std::memset(&pk, 0, sizeof(pk));
+        for (int si = 0; si < ns; ++si) {
+            pk.M[si] = pl->d_M[si] + L.m_off[si][i];
+            pk.n_cells[si] = n_cells(bN, pl->prm.stages[si]);
+        }
+        pk.theta = pl->d_theta + (size_t)i * JERK_MAX_STAGES;
+        pk.n_stages = ns;
+        pk.item = i;
+        pk.out = pl->d_cand;
+        pk.cap = pl->prm.max_candidates;
+        pk.count = pl->d_count;
+        JCHECK(launch_peaks(pk, st));
+    }
+    JCHECK(mark(pl, 5, st, capturing));
+    return JERK_OK;
 }
 
 // after a synchronisation point: did a bounded device wait expire?
@@ -277,6 +462,14 @@ jerk_status device_error(jerk_plan_s *pl) {
         cudaMemset(pl->d_err, 0, sizeof(int));
         return JERK_ETIMEOUT;
     }
+    return JERK_OK;
+}
+
+jerk_status finish_search(jerk_plan_s *pl, cudaStream_t st, int count, bool profiled) {
+    JCHECK(cudaEventRecord(pl->done, st));
+    pl->last_count = count;
+    pl->searched = true;
+    pl->profiled = profiled;
     return JERK_OK;
 }
 
@@ -310,6 +503,7 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     if (!pl) return JERK_ENOMEM;
     pl->prm = *params;
     pl->device = device;
+    pl->max_batch = std::max(1, params->max_batch);
     pl->b = params->numbetween;
     pl->nz = 2 * params->zmax / params->dz + 1;
     pl->nw = 2 * params->wmax / params->dw + 1;
@@ -355,11 +549,14 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
 
     const int64_t N = params->max_bins, bN = (int64_t)pl->b * N;
     const int ns = params->n_stages;
-    pl->slot_cap = build_tables(pl, N, false);
+    build_row_structure(pl);
     build_groups(pl, tpg_for(pl, nseg_for(pl, N), pl->T));
-    // the conv grid only grows with n
-    const int64_t conv_blocks = group_ctas(pl, N, nullptr);
-    const int64_t harm_blocks = ns > 1 ? (n_cells(bN, params->stages[1]) + 255) / 256 : 0;
+    // capacities for any set of at most max_batch spectra totalling at most N bins
+    // (rows, CTAs and harmonic blocks grow with n; each extra spectrum adds rounding)
+    pl->slot_cap = item_rows(pl, N, 0, nullptr, nullptr, nullptr) +
+                   (int64_t)pl->max_batch * 32 * std::max(1, pl->n_fund * JERK_MAX_HARMONIC);
+    const int64_t conv_blocks = ctas_for(pl, N) + (int64_t)pl->max_batch * (int64_t)pl->groups.size();
+    const int64_t harm_blocks = harm_blocks_for(pl, N) + pl->max_batch;
     pl->stat_part_cap = 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
 
     // does it fit?
@@ -367,7 +564,7 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     JCHECK(cudaMemGetInfo(&free_b, &total_b));
     int64_t need = (int64_t)pl->T * pl->L * 8 + 2 * N * 8 + pl->slot_cap * 4 + pl->stat_part_cap * 8 +
                    params->max_candidates * (int64_t)sizeof(DevCand) + (int64_t)pl->T * 40;
-    for (int si = 0; si < ns; ++si) need += n_cells(bN, params->stages[si]) * 8;
+    for (int si = 0; si < ns; ++si) need += (n_cells(bN, params->stages[si]) + pl->max_batch) * 8;
     if ((double)need > 0.97 * (double)free_b) {
         delete pl;
         return JERK_ENOMEM;
@@ -379,25 +576,18 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     TRY(dalloc(pl, &pl->d_bank, (size_t)pl->T * pl->L));
     TRY(dalloc(pl, &pl->d_spec_in, (size_t)N));
     TRY(dalloc(pl, &pl->d_spec_norm, (size_t)N));
-    for (int si = 0; si < ns; ++si) TRY(dalloc(pl, &pl->d_M[si], (size_t)n_cells(bN, params->stages[si])));
+    for (int si = 0; si < ns; ++si)
+        TRY(dalloc(pl, &pl->d_M[si], (size_t)(n_cells(bN, params->stages[si]) + pl->max_batch)));
     TRY(dalloc(pl, &pl->d_slots, (size_t)pl->slot_cap));
     TRY(dalloc(pl, &pl->d_zt, (size_t)pl->T));
     TRY(dalloc(pl, &pl->d_order, (size_t)pl->T));
-    TRY(dalloc(pl, &pl->d_groups, pl->groups.size() + 1));
     TRY(dalloc(pl, &pl->d_wt, (size_t)pl->T));
     TRY(dalloc(pl, &pl->d_slot_beg, (size_t)pl->T + 1));
-    // entry / fundamental counts do not depend on n
-    build_tables(pl, N, true);
-    pl->tables_n = -1;
     TRY(dalloc(pl, &pl->d_slot_h, (size_t)pl->n_entries));
-    TRY(dalloc(pl, &pl->d_slot_off, (size_t)pl->n_entries));
-    TRY(dalloc(pl, &pl->d_slot_len, (size_t)pl->n_entries));
-    TRY(dalloc(pl, &pl->d_fund, (size_t)pl->n_fund));
     TRY(dalloc(pl, &pl->d_stat_part, (size_t)pl->stat_part_cap));
-    TRY(dalloc(pl, &pl->d_stats, (size_t)2 * JERK_MAX_STAGES));
-    TRY(dalloc(pl, &pl->d_counts, (size_t)JERK_MAX_STAGES));
+    TRY(dalloc(pl, &pl->d_stats, (size_t)2 * JERK_MAX_STAGES * pl->max_batch));
     TRY(dalloc(pl, &pl->d_thresh, (size_t)JERK_MAX_STAGES));
-    TRY(dalloc(pl, &pl->d_theta, (size_t)JERK_MAX_STAGES));
+    TRY(dalloc(pl, &pl->d_theta, (size_t)JERK_MAX_STAGES * pl->max_batch));
     TRY(dalloc(pl, &pl->d_cand, (size_t)params->max_candidates));
     TRY(dalloc(pl, &pl->d_count, 1));
     TRY(dalloc(pl, &pl->d_err, 1));
@@ -408,6 +598,9 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     TRY(cudaMemcpy(pl->d_zt, pl->zt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(pl->d_order, pl->order.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(pl->d_wt, pl->wt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(pl->d_slot_beg, pl->h_slot_beg.data(), sizeof(int32_t) * (pl->T + 1), cudaMemcpyHostToDevice));
+    if (pl->n_entries)
+        TRY(cudaMemcpy(pl->d_slot_h, pl->h_slot_h.data(), sizeof(int32_t) * pl->n_entries, cudaMemcpyHostToDevice));
     TRY(cudaMemcpy(pl->d_thresh, params->thresh, sizeof(float) * JERK_MAX_STAGES, cudaMemcpyHostToDevice));
     if (e == cudaSuccess) {
         std::vector<double> x, w;
@@ -538,29 +731,28 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
     JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
-    cudaError_t e;
-    const float2 *spec = normalised_input(pl, d_spec, n, st, &e);
-    JCHECK(e);
     {
-        const jerk_status ts = ensure_tables(pl, n, st);
-        if (ts != JERK_OK) return ts;
+        const jerk_status ls = ensure_layout(pl, std::vector<int64_t>{n}, st);
+        if (ls != JERK_OK) return ls;
     }
+    if (pl->prm.norm_block > 0)
+        JCHECK(launch_normalise((const float2 *)d_spec, pl->d_spec_norm, n, pl->prm.norm_block, st));
+    else
+        JCHECK(cudaMemcpyAsync(pl->d_spec_norm, d_spec, sizeof(float2) * n, cudaMemcpyDeviceToDevice, st));
     ConvArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.spec = spec;
-    a.N = n;
-    a.bN = (int64_t)pl->b * n;
+    a.items = pl->lay.d_items;
     a.bank = pl->d_bank;
     a.order = pl->d_order;
-    a.grp = pl->d_groups;
-    a.n_groups = (int32_t)pl->groups.size();
+    a.grp = pl->lay.d_work;
+    a.n_work = pl->lay.n_work;
     a.T = pl->T;
     a.t0 = t0;
     a.nt = nt;
     a.plane = d_out;
     a.err = pl->d_err;
     a.slot_beg = pl->d_slot_beg;
-    JCHECK(launch_conv(pl->log2L, 1, false, a, (int)pl->conv_ctas, st));
+    JCHECK(launch_conv(pl->log2L, 1, false, a, (int)pl->lay.total_ctas, st));
     JCHECK(cudaEventRecord(pl->done, st));
     return JERK_OK;
 }
@@ -571,100 +763,68 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
     JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
-    jerk_status s = ensure_tables(pl, n, st);
+    jerk_status s = ensure_layout(pl, std::vector<int64_t>{n}, st);
     if (s != JERK_OK) return s;
-    const int ns = pl->prm.n_stages;
-    const int64_t bN = (int64_t)pl->b * n;
-    const bool sigma = pl->prm.thresh_mode == JERK_THRESH_SIGMA;
+    const float2 *in[1] = {(const float2 *)d_spec};
+    s = enqueue_search(pl, in, st, false);
+    if (s != JERK_OK) return s;
+    return finish_search(pl, st, 1, pl->profile);
+}
 
-    cudaError_t e;
-    JCHECK(mark(pl, 0, st));
-    const float2 *spec = normalised_input(pl, d_spec, n, st, &e);
-    JCHECK(e);
-    for (int si = 0; si < ns; ++si)
-        JCHECK(cudaMemsetAsync(pl->d_M[si], 0, sizeof(unsigned long long) * n_cells(bN, pl->prm.stages[si]), st));
-    JCHECK(mark(pl, 1, st));
-
-    // fused overlap-and-save + stage-1 max-projection + harmonic rows
-    ConvArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.spec = spec;
-    a.N = n;
-    a.bN = bN;
-    a.bank = pl->d_bank;
-    a.order = pl->d_order;
-    a.grp = pl->d_groups;
-    a.n_groups = (int32_t)pl->groups.size();
-    a.T = pl->T;
-    a.t0 = 0;
-    a.nt = pl->T;
-    a.M1 = pl->d_M[0];
-    a.slot_beg = pl->d_slot_beg;
-    a.slot_h = pl->d_slot_h;
-    a.slot_off = pl->d_slot_off;
-    a.slot_len = pl->d_slot_len;
-    a.slots = pl->d_slots;
-    a.stat_part = pl->d_stat_part;
-    a.err = pl->d_err;
-    const int64_t n1 = pl->conv_ctas;
-    JCHECK(launch_conv(pl->log2L, 0, sigma, a, (int)pl->conv_ctas, st));
-    JCHECK(mark(pl, 2, st));
-
-    // harmonic sums for stages > 1
-    int64_t nH = 0;
-    double *partH = pl->d_stat_part + 2 * n1;
-    double counts[JERK_MAX_STAGES] = {0, 0, 0, 0};
-    counts[0] = (double)bN * pl->T;
-    if (ns > 1) {
-        HarmArgs h;
-        std::memset(&h, 0, sizeof(h));
-        h.slots = pl->d_slots;
-        h.fund = pl->d_fund;
-        h.n_fund = pl->n_fund;
-        h.n_stages = ns;
-        for (int si = 0; si < ns; ++si) {
-            h.stages[si] = pl->prm.stages[si];
-            h.n_cells[si] = n_cells(bN, pl->prm.stages[si]);
-            h.M[si] = pl->d_M[si];
+jerk_status jerk_search_batch(jerk_plan pl, const void *const *d_specs, const int64_t *n, int32_t count,
+                              int32_t flags, void *stream) {
+    if (!pl || !d_specs || !n || count < 1 || count > pl->max_batch) return JERK_EINVAL;
+    if (flags & ~JERK_BATCH_GRAPH) return JERK_EINVAL;
+    int64_t total = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!d_specs[i] || n[i] < 1) return JERK_EINVAL;
+        total += n[i];
+    }
+    if (total > pl->prm.max_bins) return JERK_EINVAL;
+    if (!pl->templates_ready) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    jerk_status s = ensure_layout(pl, std::vector<int64_t>(n, n + count), st);
+    if (s != JERK_OK) return s;
+    if (!(flags & JERK_BATCH_GRAPH)) {
+        std::vector<const float2 *> in(count);
+        for (int i = 0; i < count; ++i) in[i] = (const float2 *)d_specs[i];
+        s = enqueue_search(pl, in.data(), st, false);
+        if (s != JERK_OK) return s;
+        return finish_search(pl, st, count, pl->profile);
+    }
+    // graph mode: the graph reads the spectra from the plan's input buffer,
+    // so the caller's buffers may change from call to call
+    BatchLayout &L = pl->lay;
+    std::vector<const float2 *> in(count);
+    for (int i = 0; i < count; ++i) {
+        float2 *dst = pl->d_spec_in + L.spec_off[i];
+        JCHECK(cudaMemcpyAsync(dst, d_specs[i], sizeof(float2) * n[i], cudaMemcpyDeviceToDevice, st));
+        in[i] = dst;
+    }
+    if (!L.graph) {
+        // capture on a private stream (the caller's may be the legacy default
+        // stream, which cannot be captured); the graph is launched on `st`
+        if (!pl->cap_stream) JCHECK(cudaStreamCreateWithFlags(&pl->cap_stream, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        JCHECK(cudaStreamBeginCapture(pl->cap_stream, cudaStreamCaptureModeThreadLocal));
+        s = enqueue_search(pl, in.data(), pl->cap_stream, true);
+        cudaError_t ce = cudaStreamEndCapture(pl->cap_stream, &g);
+        if (s != JERK_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
         }
-        h.stat_part = partH;
-        h.f_chunk = pl->n_fund;
-        const int64_t nthreads = (h.n_cells[1] + 3) / 4;   // 4 cells per thread
-        nH = (nthreads + 255) / 256;
-        JCHECK(launch_harmonic(h, nthreads, 1, sigma, st));
-        for (int si = 1; si < ns; ++si) {
-            int64_t nf = 0;
-            for (const auto &fe : pl->h_fund)
-                if (fe.top_stage >= si) ++nf;
-            counts[si] = (double)nf * h.n_cells[si];
+        if (ce != cudaSuccess) return from_cuda(ce);
+        ce = cudaGraphInstantiate(&L.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            L.graph = nullptr;
+            return from_cuda(ce);
         }
     }
-    JCHECK(mark(pl, 3, st));
-    JCHECK(cudaMemcpyAsync(pl->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, st));
-    JCHECK(launch_finalise_stats(pl->d_stat_part, n1, partH, nH, ns, pl->d_counts, pl->d_thresh,
-                                 pl->prm.thresh_mode, pl->d_stats, pl->d_theta, st));
-
-    // peaks
-    JCHECK(mark(pl, 4, st));
-    JCHECK(cudaMemsetAsync(pl->d_count, 0, sizeof(unsigned long long), st));
-    PeakArgs pk;
-    std::memset(&pk, 0, sizeof(pk));
-    for (int si = 0; si < ns; ++si) {
-        pk.M[si] = pl->d_M[si];
-        pk.n_cells[si] = n_cells(bN, pl->prm.stages[si]);
-    }
-    pk.theta = pl->d_theta;
-    pk.n_stages = ns;
-    pk.out = pl->d_cand;
-    pk.cap = pl->prm.max_candidates;
-    pk.count = pl->d_count;
-    JCHECK(launch_peaks(pk, st));
-    JCHECK(mark(pl, 5, st));
-    JCHECK(cudaEventRecord(pl->done, st));
-    pl->last_n = n;
-    pl->searched = true;
-    pl->profiled = pl->profile;
-    return JERK_OK;
+    JCHECK(cudaGraphLaunch(L.graph, st));
+    return finish_search(pl, st, count, false);
 }
 
 jerk_status jerk_search_host(jerk_plan pl, const void *h_spec, int64_t n, void *stream) {
@@ -693,6 +853,7 @@ jerk_status jerk_candidates(jerk_plan pl, jerk_candidate *h_out, int64_t cap, in
         JCHECK(cudaMemcpy(pl->h_cand, pl->d_cand, sizeof(DevCand) * (size_t)kept, cudaMemcpyDeviceToHost));
     std::vector<DevCand> v(pl->h_cand, pl->h_cand + kept);
     std::sort(v.begin(), v.end(), [](const DevCand &x, const DevCand &y) {
+        if (x.item != y.item) return x.item < y.item;
         return x.stage_idx != y.stage_idx ? x.stage_idx < y.stage_idx : x.p < y.p;
     });
     const int64_t ncopy = std::min<int64_t>(kept, cap);
@@ -709,18 +870,20 @@ jerk_status jerk_candidates(jerk_plan pl, jerk_candidate *h_out, int64_t cap, in
         c.z = (t >= 0 && t < pl->T) ? (float)pl->zt[t] : 0.f;
         c.w = (t >= 0 && t < pl->T) ? (float)pl->wt[t] : 0.f;
         c.power = d.power;
-        c.reserved = 0;
+        c.item = d.item;
     }
     *n_out = (int64_t)cnt;
     if ((int64_t)cnt > pl->prm.max_candidates || (int64_t)cnt > cap) return JERK_EOVERFLOW;
     return JERK_OK;
 }
 
-jerk_status jerk_maxproj(jerk_plan pl, int32_t stage_idx, const uint64_t **d_out, int64_t *n_cells_out) {
+jerk_status jerk_maxproj(jerk_plan pl, int32_t item, int32_t stage_idx, const uint64_t **d_out,
+                         int64_t *n_cells_out) {
     if (!pl || !d_out || !n_cells_out || stage_idx < 0 || stage_idx >= pl->prm.n_stages) return JERK_EINVAL;
     if (!pl->searched) return JERK_ESTATE;
-    *d_out = (const uint64_t *)pl->d_M[stage_idx];
-    *n_cells_out = n_cells((int64_t)pl->b * pl->last_n, pl->prm.stages[stage_idx]);
+    if (item < 0 || item >= pl->last_count || item >= (int)pl->lay.n.size()) return JERK_EINVAL;
+    *d_out = (const uint64_t *)(pl->d_M[stage_idx] + pl->lay.m_off[stage_idx][item]);
+    *n_cells_out = n_cells((int64_t)pl->b * pl->lay.n[item], pl->prm.stages[stage_idx]);
     return JERK_OK;
 }
 
@@ -742,9 +905,10 @@ jerk_status jerk_phase_times(jerk_plan pl, float *h_ms, int32_t n) {
     return JERK_OK;
 }
 
-jerk_status jerk_stats(jerk_plan pl, double *h_mean, double *h_std, float *h_theta) {
+jerk_status jerk_stats(jerk_plan pl, int32_t item, double *h_mean, double *h_std, float *h_theta) {
     if (!pl) return JERK_EINVAL;
     if (!pl->searched) return JERK_ESTATE;
+    if (item < 0 || item >= pl->last_count) return JERK_EINVAL;
     JCHECK(cudaSetDevice(pl->device));
     JCHECK(cudaEventSynchronize(pl->done));
     {
@@ -753,8 +917,8 @@ jerk_status jerk_stats(jerk_plan pl, double *h_mean, double *h_std, float *h_the
     }
     double st[2 * JERK_MAX_STAGES];
     float th[JERK_MAX_STAGES];
-    JCHECK(cudaMemcpy(st, pl->d_stats, sizeof(st), cudaMemcpyDeviceToHost));
-    JCHECK(cudaMemcpy(th, pl->d_theta, sizeof(th), cudaMemcpyDeviceToHost));
+    JCHECK(cudaMemcpy(st, pl->d_stats + (size_t)item * 2 * JERK_MAX_STAGES, sizeof(st), cudaMemcpyDeviceToHost));
+    JCHECK(cudaMemcpy(th, pl->d_theta + (size_t)item * JERK_MAX_STAGES, sizeof(th), cudaMemcpyDeviceToHost));
     for (int si = 0; si < pl->prm.n_stages; ++si) {
         if (h_mean) h_mean[si] = st[2 * si];
         if (h_std) h_std[si] = st[2 * si + 1];

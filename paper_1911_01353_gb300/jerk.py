@@ -19,7 +19,7 @@ JERK_OK, JERK_EINVAL, JERK_ENOMEM, JERK_ECUDA, JERK_ETIMEOUT, JERK_EOVERFLOW, JE
 THRESH_ABS, THRESH_SIGMA = 0, 1
 
 # Every function the header declares (kept in step with include/jerk.h).
-EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host",
+EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host", "jerk_search_batch",
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row")
@@ -34,14 +34,15 @@ class Params(ctypes.Structure):
                 ("stages", ctypes.c_int32 * 4), ("thresh_mode", ctypes.c_int32),
                 ("thresh", ctypes.c_float * 4), ("norm_block", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_bins", ctypes.c_int64),
-                ("max_candidates", ctypes.c_int64)]
+                ("max_candidates", ctypes.c_int64), ("max_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Candidate(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int64), ("r", ctypes.c_double), ("t", ctypes.c_int32),
                 ("z_idx", ctypes.c_int32), ("w_idx", ctypes.c_int32), ("stage", ctypes.c_int32),
                 ("z", ctypes.c_float), ("w", ctypes.c_float), ("power", ctypes.c_float),
-                ("reserved", ctypes.c_int32)]
+                ("item", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -71,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "jerk_templates": ([vp, vp], st),
             "jerk_search": ([vp, vp, i64, vp], st),
             "jerk_search_host": ([vp, vp, i64, vp], st),
+            "jerk_search_batch": ([vp, ctypes.POINTER(vp), ctypes.POINTER(i64), i32, i32, vp], st),
             "jerk_candidates": ([vp, ctypes.POINTER(Candidate), i64, ctypes.POINTER(i64)], st),
             "jerk_plan_destroy": ([vp], st),
             "jerk_status_str": ([st], ctypes.c_char_p),
@@ -78,8 +80,8 @@ def lib() -> ctypes.CDLL:
             "jerk_normalise": ([vp, vp, i64, vp, vp], st),
             "jerk_taps": ([vp, i32, i32, vp, vp], st),
             "jerk_plane": ([vp, vp, i64, i32, i32, vp, vp], st),
-            "jerk_maxproj": ([vp, i32, ctypes.POINTER(vp), ctypes.POINTER(i64)], st),
-            "jerk_stats": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+            "jerk_maxproj": ([vp, i32, i32, ctypes.POINTER(vp), ctypes.POINTER(i64)], st),
+            "jerk_stats": ([vp, i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                             ctypes.POINTER(ctypes.c_float)], st),
             "jerk_profile": ([vp, i32], st),
             "jerk_phase_times": ([vp, ctypes.POINTER(ctypes.c_float), i32], st),
@@ -116,7 +118,7 @@ def _stream_handle(stream):
 
 def make_params(zmax, dz, wmax, dw, stages=(1, 2), thresh=(15.0, 20.0), thresh_mode=THRESH_ABS,
                 pad_bins=16, seg_len=0, norm_block=1024, max_bins=1 << 16, max_candidates=1 << 16,
-                numbetween=2, precision=0) -> Params:
+                numbetween=2, precision=0, max_batch=1) -> Params:
     p = Params()
     p.zmax, p.dz, p.wmax, p.dw = zmax, dz, wmax, dw
     p.numbetween, p.pad_bins, p.seg_len = numbetween, pad_bins, seg_len
@@ -127,12 +129,14 @@ def make_params(zmax, dz, wmax, dw, stages=(1, 2), thresh=(15.0, 20.0), thresh_m
     p.thresh_mode = thresh_mode
     p.norm_block, p.precision = norm_block, precision
     p.max_bins, p.max_candidates = max_bins, max_candidates
+    p.max_batch, p.reserved = max_batch, 0
     return p
 
 
 CANDIDATE_DTYPE = np.dtype([("p", "<i8"), ("r", "<f8"), ("t", "<i4"), ("z_idx", "<i4"), ("w_idx", "<i4"),
                             ("stage", "<i4"), ("z", "<f4"), ("w", "<f4"), ("power", "<f4"),
-                            ("reserved", "<i4")])
+                            ("item", "<i4")])
+BATCH_GRAPH = 1
 
 
 def peaks_noalloc(d_maxproj: int, n_cells: int, theta: float, stage: int, zmax: int, dz: int, wmax: int,
@@ -186,6 +190,15 @@ class Plan:
         _check(lib().jerk_search(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(),
                                  _stream_handle(stream)), "jerk_search")
 
+    def search_batch(self, specs, graph: bool = False, stream=None):
+        """Enqueue one batched search of several complex64 CUDA tensors."""
+        n = len(specs)
+        ptrs = (ctypes.c_void_p * n)(*[ctypes.c_void_p(s.data_ptr()) for s in specs])
+        lens = (ctypes.c_int64 * n)(*[s.numel() for s in specs])
+        self._batch_ref = specs
+        _check(lib().jerk_search_batch(self._h, ptrs, lens, n, BATCH_GRAPH if graph else 0,
+                                       _stream_handle(stream)), "jerk_search_batch")
+
     def search_host(self, spec: np.ndarray, stream=None):
         """Enqueue a search of a host complex64 array (copied by the library)."""
         a = np.ascontiguousarray(spec, dtype=np.complex64)
@@ -207,12 +220,12 @@ class Plan:
             raise JerkError(code, "jerk_candidates (%d found)" % n.value)
         return [buf[i] for i in range(n.value)]
 
-    def stats(self):
+    def stats(self, item: int = 0):
         k = int(self.params.n_stages)
         mu = (ctypes.c_double * k)()
         sd = (ctypes.c_double * k)()
         th = (ctypes.c_float * k)()
-        _check(lib().jerk_stats(self._h, mu, sd, th), "jerk_stats")
+        _check(lib().jerk_stats(self._h, item, mu, sd, th), "jerk_stats")
         return list(mu), list(sd), list(th)
 
     def template_row(self, t: int):
@@ -247,16 +260,16 @@ class Plan:
         _check(lib().jerk_plane(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(), t0, nt,
                                 ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "jerk_plane")
 
-    def maxproj_ptr(self, stage_idx: int):
+    def maxproj_ptr(self, stage_idx: int, item: int = 0):
         ptr = ctypes.c_void_p()
         n = ctypes.c_int64()
-        _check(lib().jerk_maxproj(self._h, stage_idx, ctypes.byref(ptr), ctypes.byref(n)), "jerk_maxproj")
+        _check(lib().jerk_maxproj(self._h, item, stage_idx, ctypes.byref(ptr), ctypes.byref(n)), "jerk_maxproj")
         return ptr.value, n.value
 
-    def maxproj(self, stage_idx: int):
+    def maxproj(self, stage_idx: int, item: int = 0):
         """Copy the packed stage max-projection to host: (float32 M, int64 t)."""
         import torch
-        ptr, n = self.maxproj_ptr(stage_idx)
+        ptr, n = self.maxproj_ptr(stage_idx, item)
         dev = torch.as_tensor(_DevArray(ptr, n, "<i8"), device="cuda:%d" % self.device)
         torch.cuda.synchronize(self.device)
         host = dev.cpu().numpy().view(np.uint64)
