@@ -46,7 +46,11 @@ def args_():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("paper", "small"), default="paper")
+    ap.add_argument("--workload", choices=("paper", "small", "dm"), default="paper",
+                    help="paper: one 2^22-bin spectrum; small: 2^16 bins; dm: 64 uneven DM-trial spectra "
+                         "searched in batches (the batched form) and one by one (the per-spectrum form)")
+    ap.add_argument("--dm-count", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true", help="pick the segment length by timing (cached)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seg-len", type=int, default=0)
     ap.add_argument("--bins", type=int, default=1 << 22,
@@ -217,8 +221,95 @@ def reference_arm(a):
 # our arm
 # ---------------------------------------------------------------------------
 
+def dm_bench(a):
+    """64 DM-trial spectra of lengths 2^U(20,22) (zmax 200, wmax 300, stages
+    1-2-4-8, SIGMA thresholds): the batched form (jerk_search_batch with graph
+    replay, spectra packed into batches of at most 2^23 bins) against the
+    per-spectrum form (jerk_search on each), same plan, same candidates."""
+    import numpy as np
+    import torch
+
+    import paper_1911_01353_gb300 as pkg
+    import synth
+    from paper_1911_01353_gb300 import autotune
+    from paper_1911_01353_gb300 import build as pkg_build
+    pkg_build.build()
+    torch.cuda.set_device(0)
+    trials = synth.dm_trials(a.dm_count, seed=3)
+    specs = [synth.spectrum(n, seed, sigs) for n, seed, sigs in trials]
+    zmax, dz, wmax, dw, stages = 200, 2, 300, 20, (1, 2, 4, 8)
+    max_bins = 1 << 23
+    seg_len = autotune.best_seg_len(zmax, dz, wmax, dw, stages, 1 << 21) if a.autotune else 0
+    p = pkg.make_params(zmax, dz, wmax, dw, stages=stages, thresh=SIGMA_T, thresh_mode=pkg.THRESH_SIGMA,
+                        seg_len=seg_len, max_bins=max_bins, max_candidates=1 << 22, max_batch=16)
+    plan = pkg.Plan(p)
+    dev = [torch.from_numpy(s).cuda() for s in specs]
+    batches, cur, tot = [], [], 0
+    for i, s in enumerate(specs):
+        if cur and (tot + s.size > max_bins or len(cur) == 16):
+            batches.append(cur)
+            cur, tot = [], 0
+        cur.append(i)
+        tot += s.size
+    batches.append(cur)
+    cells = sum(2 * s.size for s in specs) * plan.info.n_templates
+    stream = torch.cuda.current_stream()
+
+    def batched():
+        out = []
+        for bt in batches:
+            plan.search_batch([dev[i] for i in bt], graph=True)
+            out += [(bt[c.item], c.stage, c.p, c.t, c.power) for c in plan.candidates()]
+        return out
+
+    def single():
+        out = []
+        for i in range(len(specs)):
+            plan.search(dev[i])
+            out += [(i, c.stage, c.p, c.t, c.power) for c in plan.candidates()]
+        return out
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    for _ in range(max(1, a.warmup)):
+        batched()
+        single()
+    tb_ms, tsingle_ms = [], []
+    rb = rs = None
+    for _ in range(a.steps):
+        t, rb = timed(batched)
+        tb_ms.append(t)
+        t, rs = timed(single)
+        tsingle_ms.append(t)
+    same = sorted(rb) == sorted(rs)
+    vb = cells / (statistics.median(tb_ms) / 1e3)
+    vs = cells / (statistics.median(tsingle_ms) / 1e3)
+    line = {"metric": METRIC, "value": vb, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": statistics.median(tb_ms), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "%d DM-trial spectra of 2^U(20,22) bins, zmax 200, wmax 300, %d templates, "
+                                   "stages 1-2-4-8" % (len(specs), plan.info.n_templates),
+                       "total_bins": int(sum(s.size for s in specs)), "batches": len(batches),
+                       "seg_len": plan.info.seg_len, "graph": True},
+            "per_spectrum_form": {"value": vs, "unit": UNIT, "ms": statistics.median(tsingle_ms)},
+            "batched_over_per_spectrum": vb / vs,
+            "candidates": len(rb), "identical_candidates": same}
+    print(json.dumps(line))
+    plan.close()
+
+
 def main():
     a = args_()
+    if a.workload == "dm" and a.impl == "ours":
+        dm_bench(a)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

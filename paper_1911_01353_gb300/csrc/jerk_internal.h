@@ -121,6 +121,7 @@ struct BatchLayout {
     jerk::FundEntry *d_fund = nullptr;             // [count][n_fund]
     double *d_counts = nullptr;                    // [count][JERK_MAX_STAGES]
     cudaGraphExec_t graph = nullptr;               // captured batch sequence
+    uint64_t last_use = 0;                         // LRU stamp
 };
 
 struct jerk_plan_s {
@@ -149,7 +150,9 @@ struct jerk_plan_s {
     std::vector<int32_t> ent_f, ent_h, fund_t, fund_top;
     std::vector<int32_t> fh_entry;     // [n_fund][JERK_MAX_HARMONIC] -> entry (or -1)
     int32_t max_batch = 1;
-    BatchLayout lay;                   // tables of the last set of lengths
+    std::vector<BatchLayout *> layouts;   // tables of recently used sets of lengths (LRU)
+    BatchLayout *cur = nullptr;           // tables of the last search
+    uint64_t use_clock = 0;
     cudaStream_t cap_stream = nullptr; // private stream graphs are captured on
     double *d_stat_part = nullptr;     // conv partials then harmonic partials
     int64_t stat_part_cap = 0;         // doubles

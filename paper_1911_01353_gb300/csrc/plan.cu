@@ -213,6 +213,8 @@ cudaError_t dalloc(jerk_plan_s *pl, T **ptr, size_t count) {
     return e;
 }
 
+constexpr size_t kMaxLayouts = 128;
+
 void free_layout(BatchLayout &L) {
     if (L.graph) cudaGraphExecDestroy(L.graph);
     cudaFree(L.d_items);
@@ -225,7 +227,12 @@ void free_layout(BatchLayout &L) {
 }
 
 void release(jerk_plan_s *pl) {
-    free_layout(pl->lay);
+    for (BatchLayout *L : pl->layouts) {
+        free_layout(*L);
+        delete L;
+    }
+    pl->layouts.clear();
+    pl->cur = nullptr;
     cudaFree(pl->d_bank);
     cudaFree(pl->d_spec_in);
     cudaFree(pl->d_spec_norm);
@@ -256,13 +263,41 @@ cudaError_t mark(jerk_plan_s *pl, int i, cudaStream_t st, bool capturing) {
     return (pl->profile && !capturing) ? cudaEventRecord(pl->ev[i], st) : cudaSuccess;
 }
 
-// Launch tables for a set of spectrum lengths (rebuilt when the set changes;
-// the host-to-device copies are synchronous).
+jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n);
+
+// Launch tables for a set of spectrum lengths: reused from a small LRU cache,
+// built on first use (a host synchronisation).
 jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaStream_t st) {
-    if (pl->lay.n == n && pl->lay.d_items) return JERK_OK;
+    for (BatchLayout *L : pl->layouts)
+        if (L->n == n) {
+            L->last_use = ++pl->use_clock;
+            pl->cur = L;
+            return JERK_OK;
+        }
     JCHECK(cudaStreamSynchronize(st));
-    free_layout(pl->lay);
-    BatchLayout &L = pl->lay;
+    BatchLayout *L = nullptr;
+    if (pl->layouts.size() >= kMaxLayouts) {
+        L = *std::min_element(pl->layouts.begin(), pl->layouts.end(),
+                              [](const BatchLayout *x, const BatchLayout *y) { return x->last_use < y->last_use; });
+        free_layout(*L);
+    } else {
+        L = new (std::nothrow) BatchLayout();
+        if (!L) return JERK_ENOMEM;
+        pl->layouts.push_back(L);
+    }
+    const jerk_status s = build_layout(pl, *L, n);
+    if (s != JERK_OK) {
+        pl->layouts.erase(std::find(pl->layouts.begin(), pl->layouts.end(), L));
+        delete L;
+        if (pl->cur == L) pl->cur = nullptr;
+        return s;
+    }
+    L->last_use = ++pl->use_clock;
+    pl->cur = L;
+    return JERK_OK;
+}
+
+jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n) {
     const int count = (int)n.size();
     const int ns = pl->prm.n_stages;
     L.n = n;
@@ -315,12 +350,12 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaSt
     // capacity checks (the plan was sized for max_bins bins in total)
     if (spec > pl->prm.max_bins || L.slot_base[count] > pl->slot_cap ||
         2 * (L.total_ctas + (int64_t)ns * L.harm0[count]) > pl->stat_part_cap) {
-        free_layout(pl->lay);
+        free_layout(L);
         return JERK_ENOMEM;
     }
     for (int si = 0; si < ns; ++si)
         if (m[si] > n_cells((int64_t)pl->b * pl->prm.max_bins, pl->prm.stages[si]) + pl->max_batch) {
-            free_layout(pl->lay);
+            free_layout(L);
             return JERK_ENOMEM;
         }
     std::vector<ItemDesc> items(count);
@@ -332,7 +367,7 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaSt
     if (e == cudaSuccess) e = cudaMalloc(&L.d_fund, sizeof(FundEntry) * fund.size());
     if (e == cudaSuccess) e = cudaMalloc(&L.d_counts, sizeof(double) * counts.size());
     if (e != cudaSuccess) {
-        free_layout(pl->lay);
+        free_layout(L);
         return from_cuda(e);
     }
     for (int i = 0; i < count; ++i) {
@@ -353,7 +388,7 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaSt
     if (e == cudaSuccess)
         e = cudaMemcpy(L.d_counts, counts.data(), sizeof(double) * counts.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        free_layout(pl->lay);
+        free_layout(L);
         return from_cuda(e);
     }
     return JERK_OK;
@@ -363,7 +398,7 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaSt
 // spectrum i (device).  Capturable into a CUDA graph (no host copies, no
 // host synchronisation, no event waits).
 jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_t st, bool capturing) {
-    const BatchLayout &L = pl->lay;
+    const BatchLayout &L = *pl->cur;
     const int count = (int)L.n.size();
     const int ns = pl->prm.n_stages;
     const bool sigma = pl->prm.thresh_mode == JERK_THRESH_SIGMA;
@@ -741,18 +776,18 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
         JCHECK(cudaMemcpyAsync(pl->d_spec_norm, d_spec, sizeof(float2) * n, cudaMemcpyDeviceToDevice, st));
     ConvArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.items = pl->lay.d_items;
+    a.items = pl->cur->d_items;
     a.bank = pl->d_bank;
     a.order = pl->d_order;
-    a.grp = pl->lay.d_work;
-    a.n_work = pl->lay.n_work;
+    a.grp = pl->cur->d_work;
+    a.n_work = pl->cur->n_work;
     a.T = pl->T;
     a.t0 = t0;
     a.nt = nt;
     a.plane = d_out;
     a.err = pl->d_err;
     a.slot_beg = pl->d_slot_beg;
-    JCHECK(launch_conv(pl->log2L, 1, false, a, (int)pl->lay.total_ctas, st));
+    JCHECK(launch_conv(pl->log2L, 1, false, a, (int)pl->cur->total_ctas, st));
     JCHECK(cudaEventRecord(pl->done, st));
     return JERK_OK;
 }
@@ -796,7 +831,7 @@ jerk_status jerk_search_batch(jerk_plan pl, const void *const *d_specs, const in
     }
     // graph mode: the graph reads the spectra from the plan's input buffer,
     // so the caller's buffers may change from call to call
-    BatchLayout &L = pl->lay;
+    BatchLayout &L = *pl->cur;
     std::vector<const float2 *> in(count);
     for (int i = 0; i < count; ++i) {
         float2 *dst = pl->d_spec_in + L.spec_off[i];
@@ -881,9 +916,9 @@ jerk_status jerk_maxproj(jerk_plan pl, int32_t item, int32_t stage_idx, const ui
                          int64_t *n_cells_out) {
     if (!pl || !d_out || !n_cells_out || stage_idx < 0 || stage_idx >= pl->prm.n_stages) return JERK_EINVAL;
     if (!pl->searched) return JERK_ESTATE;
-    if (item < 0 || item >= pl->last_count || item >= (int)pl->lay.n.size()) return JERK_EINVAL;
-    *d_out = (const uint64_t *)(pl->d_M[stage_idx] + pl->lay.m_off[stage_idx][item]);
-    *n_cells_out = n_cells((int64_t)pl->b * pl->lay.n[item], pl->prm.stages[stage_idx]);
+    if (!pl->cur || item < 0 || item >= pl->last_count || item >= (int)pl->cur->n.size()) return JERK_EINVAL;
+    *d_out = (const uint64_t *)(pl->d_M[stage_idx] + pl->cur->m_off[stage_idx][item]);
+    *n_cells_out = n_cells((int64_t)pl->b * pl->cur->n[item], pl->prm.stages[stage_idx]);
     return JERK_OK;
 }
 
