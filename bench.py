@@ -46,9 +46,13 @@ def args_():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=("paper", "small", "dm"), default="paper",
+    ap.add_argument("--workload", choices=("paper", "small", "dm", "serve"), default="paper",
                     help="paper: one 2^22-bin spectrum; small: 2^16 bins; dm: 64 uneven DM-trial spectra "
-                         "searched in batches (the batched form) and one by one (the per-spectrum form)")
+                         "searched in batches (the batched form) and one by one (the per-spectrum form); "
+                         "serve: Poisson arrivals served by the continuous-batching server and one by one")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve: arrivals per second")
+    ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
+    ap.add_argument("--workers", type=int, default=4, help="serve: plans sharing the bank")
     ap.add_argument("--dm-count", type=int, default=64)
     ap.add_argument("--autotune", action="store_true", help="pick the segment length by timing (cached)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -305,8 +309,80 @@ def dm_bench(a):
     plan.close()
 
 
+def serve_bench(a):
+    """Serving: Poisson arrivals (a.rate per second for a.duration s, seed 5)
+    of requests with lengths log-uniform in 2^18..2^23 bins, zmax in {50, 100,
+    200, 300}, wmax in {0, 300, 600, 900}; one bank for (300, 900) resident on
+    the device, stage 1 (matched filter + candidate selection, SIGMA T = 19).
+    The same trace runs through the continuous-batching server and through
+    the plain form (one request at a time, first come first served); both
+    report template-bins/s over the run and p50/p99 latency from arrival."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1911_01353_gb300 import build as pkg_build
+    from paper_1911_01353_gb300 import jerk, serve
+    pkg_build.build()
+    torch.cuda.set_device(0)
+    dz, dw = 2, 20
+    trace = serve.poisson_trace(a.rate, a.duration, seed=5)
+    warm = serve.poisson_trace(a.rate, 1.0, seed=6)
+    # four base spectra of 2^23 bins (noise + 6 chirps each); a request of n
+    # bins is the first n bins of one of them, from pinned host memory
+    rng = np.random.default_rng(5)
+    base = []
+    for k in range(4):
+        n = 1 << 23
+        sigs = [synth.Signal(float(rng.uniform(600, (1 << 18) - 600)) if i < 3 else float(rng.uniform(600, n - 600)),
+                             float(rng.uniform(-300, 300)), float(rng.uniform(-900, 900)),
+                             float(rng.uniform(30, 60)), float(rng.uniform(0, 6.28)))
+                for i in range(6)]
+        base.append(torch.from_numpy(synth.spectrum(n, 50 + k, sigs)).pin_memory())
+
+    def requests(tr, rid0=0):
+        return [serve.Request(rid0 + i, base[(rid0 + i) % 4][:n], zs, ws, arrival=t)
+                for i, (t, n, zs, ws) in enumerate(tr)]
+
+    t0 = time.perf_counter()
+    srv = serve.Server(300, 900, dz=dz, dw=dw, stages=(1,), thresh=(19.0,), thresh_mode=jerk.THRESH_SIGMA,
+                       n_workers=a.workers, worker_bins=1 << 24, max_batch=32, max_candidates=1 << 22)
+    bank_s = time.perf_counter() - t0
+    bus = getattr(torch.cuda.get_device_properties(0), "pci_bus_id", None)
+    clk = ClockSampler(str(bus) if bus is not None else None)
+    out = {}
+    for name, kw in (("served", dict()), ("plain", dict(n_workers=1, max_batch=1, fifo=True))):
+        srv.run(requests(warm, 100000), **kw)                     # warm-up
+        if name == "served":
+            clk.start()
+        done = srv.run(requests(trace), **kw)
+        if name == "served":
+            clocks = clk.stop()
+        out[name] = (serve.summary(done, dz, dw), {r.rid: r.candidates for r in done})
+    same = out["served"][1] == out["plain"][1]
+    sv, pl = out["served"][0], out["plain"][0]
+    line = {"metric": METRIC + "; p50/p99 latency", "value": sv["cells_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": sv["seconds"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serving: Poisson %.0f req/s for %.0f s, n = 2^U(18,23) bins, zmax in "
+                                   "{50,100,200,300}, wmax in {0,300,600,900}, one (300, 900) bank of %d "
+                                   "templates, stage 1" % (a.rate, a.duration, srv.bank.info.n_templates),
+                       "requests": sv["requests"], "workers": a.workers, "seg_len": srv.bank.info.seg_len,
+                       "bank_bytes": srv.bank.info.bank_bytes, "bank_build_s": bank_s},
+            "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"], "mean_ms": sv["mean_ms"],
+            "plain_form": {"value": pl["cells_per_s"], "p50_ms": pl["p50_ms"], "p99_ms": pl["p99_ms"],
+                           "seconds": pl["seconds"]},
+            "served_over_plain": sv["cells_per_s"] / pl["cells_per_s"],
+            "offered_cells_per_s": sv["cells"] / a.duration,
+            "identical_candidates": same, "clocks": clocks}
+    print(json.dumps(line))
+    srv.close()
+
+
 def main():
     a = args_()
+    if a.workload == "serve" and a.impl == "ours":
+        return serve_bench(a)
     if a.workload == "dm" and a.impl == "ours":
         dm_bench(a)
         return

@@ -56,7 +56,7 @@ typedef enum {
 
 enum { JERK_THRESH_ABS = 0, JERK_THRESH_SIGMA = 1 };
 enum { JERK_MAX_STAGES = 4, JERK_MAX_HARMONIC = 8 };
-enum { JERK_BATCH_GRAPH = 1 };
+enum { JERK_BATCH_GRAPH = 1, JERK_BATCH_TRANSIENT = 2 };
 
 /* Search parameters.  Sec. 2 defines the (z, w) filters; Sec. 3 the
  * user threshold, statistics and harmonic sum. */
@@ -100,12 +100,14 @@ typedef struct {
     int32_t device;
     int64_t max_bins;
     int64_t slot_floats;     /* harmonic-row workspace at max_bins, in floats */
-    int64_t workspace_bytes; /* device bytes the plan holds */
+    int64_t workspace_bytes; /* device bytes of the plan's own workspace (bank excluded) */
     int64_t transforms;      /* length-L inverse transforms one search of max_bins bins performs */
     int32_t n_groups;        /* template groups (similar half-width, own segment length) */
     int32_t reserved;
     const void *d_bank;      /* complex64[n_templates][L] template spectra in processing order
                                 (see jerk_template_row; valid after jerk_templates) */
+    int64_t bank_bytes;      /* device bytes of the template bank and its tables, shared by
+                                every plan made from it with jerk_plan_share */
 } jerk_info;
 
 /* Validate `params`, select device `device` (made current), size and
@@ -151,6 +153,36 @@ jerk_status jerk_search_host(jerk_plan plan, const void *h_spec, int64_t n, void
  * rebuilds the launch tables (a host synchronisation). */
 jerk_status jerk_search_batch(jerk_plan plan, const void *const *d_specs, const int64_t *n, int32_t count,
                               int32_t flags, void *stream);
+
+/* As jerk_search_batch, with spectrum i searched over the sub-grid
+ * |z| <= zmax[i], |w| <= wmax[i] of the plan's bank (host arrays; both NULL =
+ * the whole bank for every spectrum).  Each zmax[i] must be a multiple of dz
+ * in [0, plan zmax], each wmax[i] a multiple of dw in [0, plan wmax]; the
+ * harmonic sum of spectrum i follows the definition of stage H with its own
+ * zmax[i], wmax[i] (Sec. 3).  This is how one resident bank built for the
+ * largest (zmax, wmax) serves requests of any smaller search range (Sec. 2
+ * defines the filters per (z, w), so a sub-grid uses the same filters).
+ * Results equal those of the same spectrum and sub-grid searched alone on
+ * this bank; candidate t, z_idx, w_idx are indices of the bank's grid.
+ * flags: JERK_BATCH_GRAPH as for jerk_search_batch; JERK_BATCH_TRANSIENT
+ * builds the launch tables into buffers the plan allocates once, with one
+ * asynchronous upload and no device synchronisation, so searches on several
+ * plans sharing a bank overlap on the GPU (the host waits for this plan's
+ * previous search only).  The two flags exclude each other. */
+jerk_status jerk_search_batch_grid(jerk_plan plan, const void *const *d_specs, const int64_t *n, const int32_t *zmax,
+                                   const int32_t *wmax, int32_t count, int32_t flags, void *stream);
+
+/* A new plan that uses `parent`'s template bank (not copied; jerk_templates
+ * on either plan fills it for both) with its own workspace, candidate buffer
+ * and thresholds, so several searches over one bank can be in flight at once
+ * (one per plan, each on its own stream).  params must equal the parent's in
+ * zmax, dz, wmax, dw, numbetween, pad_bins, n_stages, stages and precision,
+ * and seg_len must be 0 or the parent's L; max_bins, max_candidates,
+ * max_batch, thresh_mode, thresh and norm_block may differ.  The bank stays
+ * allocated until the last plan using it is destroyed, in any order.  The
+ * plans are independent for thread-safety purposes, but jerk_templates must
+ * not run while another plan on the bank searches. */
+jerk_status jerk_plan_share(jerk_plan parent, const jerk_params *params, jerk_plan *out);
 
 /* Wait for the last search to finish and copy its candidates to h_out
  * (capacity cap records), sorted by (stage position, p).  *n_out receives

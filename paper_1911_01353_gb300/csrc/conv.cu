@@ -130,6 +130,14 @@ __device__ __forceinline__ auto make_tw(const float2 *tab, int j) {
     }
 }
 
+// Bank row (processing index) of position k of a work entry: the identity for
+// whole-bank searches, a lookup when an item searches a sub-grid of the bank.
+template <bool ROWS>
+__device__ __forceinline__ int bank_row(const ConvArgs &a, int k) {
+    if constexpr (ROWS) return __ldg(a.rows + k);
+    return k;
+}
+
 // Store the staged power row of one template into its harmonic-row slots
 // (entries e0..e1): cells q = h p of this segment, p within the row.
 __device__ __forceinline__ void store_rows(const ConvArgs &a, const int64_t *soff, const int64_t *slen,
@@ -155,7 +163,7 @@ __device__ __forceinline__ void store_rows(const ConvArgs &a, const int64_t *sof
     }
 }
 
-template <int LOG2L, int MODE, bool STATS>
+template <int LOG2L, int MODE, bool STATS, bool ROWS>
 __global__ void __launch_bounds__(ConvCfg<LOG2L>::THREADS, ConvCfg<LOG2L>::MINB)
 conv_kernel(ConvArgs a) {
     using C = FftCfg<LOG2L>;
@@ -222,7 +230,8 @@ conv_kernel(ConvArgs a) {
     if (tid == 0)
         for (int b = 0; b < NBUF && tb + b < te; ++b) {
             issued[b] = 1;
-            bulk_load(smem + b * L, a.bank + (int64_t)(tb + b) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+            bulk_load(smem + b * L, a.bank + (int64_t)bank_row<ROWS>(a, tb + b) * L, (uint32_t)(L * sizeof(float2)),
+                      &full[b]);
         }
 
     // ---- 1. forward FFT of the spread segment -------------------------------
@@ -300,7 +309,8 @@ conv_kernel(ConvArgs a) {
             rel[b] = 0;
             if (k + NBUF < te) {
                 issued[b] += 1;
-                bulk_load(smem + b * L, a.bank + (int64_t)(k + NBUF) * L, (uint32_t)(L * sizeof(float2)), &full[b]);
+                bulk_load(smem + b * L, a.bank + (int64_t)bank_row<ROWS>(a, k + NBUF) * L, (uint32_t)(L * sizeof(float2)),
+                          &full[b]);
             }
         }
         fft_store0<LOG2L>(v, work, j);
@@ -413,10 +423,10 @@ conv_kernel(ConvArgs a) {
 
 int conv_segs_per_cta(int log2L) { return log2L >= 13 ? 1 : 2; }
 
-template <int LOG2L, int MODE, bool STATS>
+template <int LOG2L, int MODE, bool STATS, bool ROWS = false>
 static cudaError_t launch_one(const ConvArgs &a, int n_ctas, cudaStream_t st) {
     using CC = ConvCfg<LOG2L>;
-    auto k = conv_kernel<LOG2L, MODE, STATS>;
+    auto k = conv_kernel<LOG2L, MODE, STATS, ROWS>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CC::SMEM);
     if (e != cudaSuccess) return e;
     k<<<n_ctas, CC::THREADS, CC::SMEM, st>>>(a);
@@ -426,6 +436,8 @@ static cudaError_t launch_one(const ConvArgs &a, int n_ctas, cudaStream_t st) {
 template <int LOG2L>
 static cudaError_t launch_L(int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st) {
     if (mode == 1) return launch_one<LOG2L, 1, false>(a, n_ctas, st);
+    if (a.rows) return stats ? launch_one<LOG2L, 0, true, true>(a, n_ctas, st)
+                             : launch_one<LOG2L, 0, false, true>(a, n_ctas, st);
     if (stats) return launch_one<LOG2L, 0, true>(a, n_ctas, st);
     return launch_one<LOG2L, 0, false>(a, n_ctas, st);
 }

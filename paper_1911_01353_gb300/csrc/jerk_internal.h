@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <memory>
 #include <vector>
 
 #include "../../include/jerk.h"
@@ -47,7 +49,10 @@ struct ItemDesc {
 struct ConvArgs {
     const ItemDesc *items;   // spectra of the launch
     const float2 *bank;      // [T][L] template spectra in processing order
-    const int32_t *order;    // processing index -> template index t
+    const int32_t *order;    // position -> template index t
+    const int32_t *rows;     // position -> bank row; null: the identity.  A work entry's
+                             // tb..te-1 are positions; when items search sub-grids of the
+                             // bank, positions list the templates inside each sub-grid
     const ConvGroup *grp;    // [n_work + 1] (item, group) entries; grp[n_work].cta0 = total CTAs
     int32_t T, n_work;
     int32_t t0, nt;          // template range written in plane mode
@@ -108,6 +113,8 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 // Launch tables of one set of spectrum lengths (a batch, or one spectrum).
 struct BatchLayout {
     std::vector<int64_t> n;                        // lengths: the cache key
+    std::vector<int32_t> zmax, wmax;               // per-item sub-grids (empty: whole bank); part of the key
+    std::vector<int32_t> n_fund;                   // [count] fundamentals of each item (stages > 1)
     int64_t total_ctas = 0;
     int n_work = 0;
     std::vector<int64_t> item_cta0;                // [count + 1] conv CTAs of each item
@@ -120,8 +127,34 @@ struct BatchLayout {
     int64_t *d_soff = nullptr, *d_slen = nullptr;  // [count][n_entries]
     jerk::FundEntry *d_fund = nullptr;             // [count][n_fund]
     double *d_counts = nullptr;                    // [count][JERK_MAX_STAGES]
+    int32_t *d_rows = nullptr;                     // position -> bank row (sub-grid layouts)
+    int32_t *d_tl = nullptr;                       // position -> template index (sub-grid layouts)
     cudaGraphExec_t graph = nullptr;               // captured batch sequence
     uint64_t last_use = 0;                         // LRU stamp
+};
+
+// Bank-level device state that plans created by jerk_plan_share use
+// together: the template spectra and the per-template tables.  Freed when the
+// last plan holding it is destroyed.
+struct BankShare {
+    int device = 0;
+    float2 *d_bank = nullptr;
+    int32_t *d_zt = nullptr, *d_wt = nullptr, *d_order = nullptr;
+    int32_t *d_slot_beg = nullptr, *d_slot_h = nullptr;
+    double2 *d_gl = nullptr;
+    int64_t bytes = 0;
+    std::atomic<bool> ready{false};   // jerk_templates has filled d_bank
+    ~BankShare();
+};
+
+// Preallocated launch tables for JERK_BATCH_TRANSIENT searches: filled from
+// pinned host staging by asynchronous copies, so a search allocates and frees
+// nothing and never synchronises the device.
+struct TransientTables {
+    int64_t cap_work = 0, cap_ent = 0, cap_fund = 0, cap_rows = 0;
+    void *h_stage = nullptr;          // pinned: items | work | soff | slen | fund | counts | rows
+    void *d_buf = nullptr;            // device copy of the same layout
+    size_t bytes = 0;
 };
 
 struct jerk_plan_s {
@@ -129,7 +162,8 @@ struct jerk_plan_s {
     int device;
     int b, nz, nw, T, M, K, L, log2L, V;
     std::vector<int32_t> zt, wt, mt;   // grid values and per-template half-width
-    // device memory
+    // device memory; the bank-level arrays belong to `share`
+    std::shared_ptr<BankShare> share;
     float2 *d_bank = nullptr;
     float2 *d_spec_in = nullptr;
     float2 *d_spec_norm = nullptr;
@@ -152,6 +186,8 @@ struct jerk_plan_s {
     int32_t max_batch = 1;
     std::vector<BatchLayout *> layouts;   // tables of recently used sets of lengths (LRU)
     BatchLayout *cur = nullptr;           // tables of the last search
+    BatchLayout transient_layout;         // host side of the transient tables
+    TransientTables tt;
     uint64_t use_clock = 0;
     cudaStream_t cap_stream = nullptr; // private stream graphs are captured on
     double *d_stat_part = nullptr;     // conv partials then harmonic partials
@@ -168,7 +204,6 @@ struct jerk_plan_s {
     int64_t bytes = 0;
     std::vector<int32_t> h_slot_beg, h_slot_h;
     // state
-    bool templates_ready = false;
     int32_t last_count = 0;            // spectra of the last search
     bool searched = false;
     cudaEvent_t done = nullptr;

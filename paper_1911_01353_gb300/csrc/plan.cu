@@ -13,6 +13,20 @@
 
 using namespace jerk;
 
+BankShare::~BankShare() {
+    int cur = -1;
+    const bool had = cudaGetDevice(&cur) == cudaSuccess;
+    cudaSetDevice(device);
+    cudaFree(d_bank);
+    cudaFree(d_zt);
+    cudaFree(d_wt);
+    cudaFree(d_order);
+    cudaFree(d_slot_beg);
+    cudaFree(d_slot_h);
+    cudaFree(d_gl);
+    if (had) cudaSetDevice(cur);
+}
+
 namespace {
 
 constexpr int kSMs = 152;
@@ -89,29 +103,53 @@ void build_row_structure(jerk_plan_s *pl) {
     for (int t = 0; t < pl->T; ++t) pl->h_slot_beg[t + 1] += pl->h_slot_beg[t];
 }
 
-// Row offsets and lengths of one spectrum of n bins whose rows start at
-// `base` (floats); returns the floats used.  Rows are 128-byte aligned.
-int64_t item_rows(const jerk_plan_s *pl, int64_t n, int64_t base, int64_t *soff, int64_t *slen, FundEntry *fund) {
+bool valid_in(const jerk_plan_s *pl, int t, int H, int zs, int ws) {
+    return (int64_t)H * std::abs(pl->zt[t]) <= zs && (int64_t)H * std::abs(pl->wt[t]) <= ws;
+}
+
+// Row offsets and lengths of one spectrum of n bins searched over the
+// sub-grid |z| <= zs, |w| <= ws, whose rows start at `base` (floats); returns
+// the floats used.  Rows are 128-byte aligned.  An entry whose fundamental is
+// not a fundamental of the sub-grid at any stage > 1, or whose harmonic lies
+// above the fundamental's top stage there, gets length 0 (the filter kernel
+// skips it).  *nf receives the fundamentals written to `fund`, nf_stage[si]
+// those valid at stage si.
+int64_t item_rows(const jerk_plan_s *pl, int64_t n, int zs, int ws, int64_t base, int64_t *soff, int64_t *slen,
+                  FundEntry *fund, int *nf, int64_t *nf_stage) {
     const int64_t bN = (int64_t)pl->b * n;
     int64_t off = base;
+    int k = 0;
     for (int f = 0; f < pl->n_fund; ++f) {
+        const int t = pl->fund_t[f];
+        int top = 0;
+        for (int si = 1; si <= pl->fund_top[f]; ++si)
+            if (valid_in(pl, t, pl->prm.stages[si], zs, ws)) top = si;
+        const int Hmaster = pl->prm.stages[pl->fund_top[f]];
+        const int Htop = top ? pl->prm.stages[top] : 0;
         FundEntry fe;
         std::memset(&fe, 0, sizeof(fe));
-        fe.t = pl->fund_t[f];
-        fe.top_stage = pl->fund_top[f];
-        const int Htop = pl->prm.stages[fe.top_stage];
-        for (int h = 1; h <= Htop; ++h) {
-            int sn = 1;
-            while (pl->prm.stages[sn] < std::max(h, 2)) ++sn;
-            const int64_t len = n_cells(bN, pl->prm.stages[sn]);
-            fe.off[h - 1] = off;
+        fe.t = t;
+        fe.top_stage = top;
+        for (int h = 1; h <= Hmaster; ++h) {
             const int e = pl->fh_entry[(size_t)f * JERK_MAX_HARMONIC + h - 1];
+            int64_t len = 0;
+            if (h <= Htop) {
+                int sn = 1;
+                while (pl->prm.stages[sn] < std::max(h, 2)) ++sn;
+                len = n_cells(bN, pl->prm.stages[sn]);
+            }
+            fe.off[h - 1] = off;
             if (soff) soff[e] = off;
             if (slen) slen[e] = len;
             off += round32(len);
         }
-        if (fund) fund[f] = fe;
+        if (top == 0) continue;
+        if (nf_stage)
+            for (int si = 1; si <= top; ++si) ++nf_stage[si];
+        if (fund) fund[k] = fe;
+        ++k;
     }
+    if (nf) *nf = k;
     return off - base;
 }
 
@@ -205,13 +243,15 @@ jerk_status validate(const jerk_params *p) {
 }
 
 template <typename T>
-cudaError_t dalloc(jerk_plan_s *pl, T **ptr, size_t count) {
+cudaError_t dalloc(int64_t *bytes, T **ptr, size_t count) {
     *ptr = nullptr;
     if (count == 0) count = 1;
     cudaError_t e = cudaMalloc((void **)ptr, count * sizeof(T));
-    if (e == cudaSuccess) pl->bytes += (int64_t)(count * sizeof(T));
+    if (e == cudaSuccess) *bytes += (int64_t)(count * sizeof(T));
     return e;
 }
+
+bool bank_ready(const jerk_plan_s *pl) { return pl->share && pl->share->ready.load(); }
 
 constexpr size_t kMaxLayouts = 128;
 
@@ -223,6 +263,8 @@ void free_layout(BatchLayout &L) {
     cudaFree(L.d_slen);
     cudaFree(L.d_fund);
     cudaFree(L.d_counts);
+    cudaFree(L.d_rows);
+    cudaFree(L.d_tl);
     L = BatchLayout();
 }
 
@@ -233,16 +275,15 @@ void release(jerk_plan_s *pl) {
     }
     pl->layouts.clear();
     pl->cur = nullptr;
-    cudaFree(pl->d_bank);
+    if (pl->tt.d_buf) cudaFree(pl->tt.d_buf);
+    if (pl->tt.h_stage) cudaFreeHost(pl->tt.h_stage);
+    pl->tt = TransientTables();
+    pl->share.reset();                 // the bank goes with the last plan using it
+    pl->d_bank = nullptr;
     cudaFree(pl->d_spec_in);
     cudaFree(pl->d_spec_norm);
     for (auto &m : pl->d_M) cudaFree(m);
     cudaFree(pl->d_slots);
-    cudaFree(pl->d_zt);
-    cudaFree(pl->d_order);
-    cudaFree(pl->d_wt);
-    cudaFree(pl->d_slot_beg);
-    cudaFree(pl->d_slot_h);
     cudaFree(pl->d_stat_part);
     cudaFree(pl->d_stats);
     cudaFree(pl->d_thresh);
@@ -250,7 +291,6 @@ void release(jerk_plan_s *pl) {
     cudaFree(pl->d_cand);
     cudaFree(pl->d_count);
     cudaFree(pl->d_err);
-    cudaFree(pl->d_gl);
     if (pl->h_cand) cudaFreeHost(pl->h_cand);
     if (pl->done) cudaEventDestroy(pl->done);
     for (auto &e : pl->ev)
@@ -263,13 +303,153 @@ cudaError_t mark(jerk_plan_s *pl, int i, cudaStream_t st, bool capturing) {
     return (pl->profile && !capturing) ? cudaEventRecord(pl->ev[i], st) : cudaSuccess;
 }
 
-jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n);
+// Host side of a batch's launch tables.  Items' device pointers are filled in
+// once the tables' device addresses are known.
+struct HostTables {
+    std::vector<ItemDesc> items;
+    std::vector<ConvGroup> work;
+    std::vector<int64_t> soff, slen;
+    std::vector<FundEntry> fund;
+    std::vector<double> counts;
+    std::vector<int32_t> rows, tl;   // sub-grid layouts: position -> bank row, template index
+};
 
-// Launch tables for a set of spectrum lengths: reused from a small LRU cache,
-// built on first use (a host synchronisation).
-jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaStream_t st) {
+// Launch tables for spectra of lengths n, item i searched over |z| <= zm[i],
+// |w| <= wm[i] (zm, wm empty: the whole bank).  Fills L's host fields and h.
+jerk_status plan_tables(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n,
+                        const std::vector<int32_t> &zm, const std::vector<int32_t> &wm, HostTables &h) {
+    const int count = (int)n.size();
+    const int ns = pl->prm.n_stages;
+    const bool sub = !zm.empty();
+    L.n = n;
+    L.zmax = zm;
+    L.wmax = wm;
+    L.total_ctas = 0;
+    L.item_cta0.assign(count + 1, 0);
+    L.harm0.assign(count + 1, 0);
+    L.spec_off.assign(count, 0);
+    L.slot_base.assign(count + 1, 0);
+    L.n_fund.assign(count, 0);
+    for (int si = 0; si < ns; ++si) L.m_off[si].assign(count, 0);
+    h.items.assign(count, ItemDesc());
+    h.soff.assign((size_t)count * std::max(pl->n_entries, 1), 0);
+    h.slen.assign(h.soff.size(), 0);
+    h.fund.assign((size_t)count * std::max(pl->n_fund, 1), FundEntry());
+    h.counts.assign((size_t)count * JERK_MAX_STAGES, 0.0);
+    h.work.clear();
+    h.rows.clear();
+    h.tl.clear();
+    int64_t spec = 0, m[JERK_MAX_STAGES] = {0, 0, 0, 0};
+    const int segs = conv_segs_per_cta(pl->log2L);
+    for (int i = 0; i < count; ++i) {
+        const int zs = sub ? zm[i] : pl->prm.zmax, ws = sub ? wm[i] : pl->prm.wmax;
+        const int64_t bN = (int64_t)pl->b * n[i];
+        L.spec_off[i] = spec;
+        spec += n[i];
+        for (int si = 0; si < ns; ++si) {
+            L.m_off[si][i] = m[si];
+            m[si] += n_cells(bN, pl->prm.stages[si]);
+        }
+        int64_t nf_stage[JERK_MAX_STAGES] = {0, 0, 0, 0};
+        int nf = 0;
+        const int64_t used = item_rows(pl, n[i], zs, ws, L.slot_base[i], h.soff.data() + (size_t)i * pl->n_entries,
+                                       h.slen.data() + (size_t)i * pl->n_entries,
+                                       h.fund.data() + (size_t)i * pl->n_fund, &nf, nf_stage);
+        L.slot_base[i + 1] = L.slot_base[i] + used;
+        L.n_fund[i] = nf;
+        // conv work: this spectrum's (group, segment range) entries, item-major;
+        // a sub-grid keeps, per group, the templates inside it (positions into `rows`)
+        int64_t nt_item = 0;
+        for (const auto &g : pl->groups) {
+            ConvGroup w = g;
+            if (sub) {
+                w.tb = (int32_t)h.rows.size();
+                for (int k = g.tb; k < g.te; ++k) {
+                    const int t = pl->order[k];
+                    if (std::abs(pl->zt[t]) <= zs && std::abs(pl->wt[t]) <= ws) {
+                        h.rows.push_back(k);
+                        h.tl.push_back(t);
+                    }
+                }
+                w.te = (int32_t)h.rows.size();
+                if (w.te == w.tb) continue;
+            }
+            nt_item += w.te - w.tb;
+            w.cta0 = (int32_t)L.total_ctas;
+            w.item = i;
+            h.work.push_back(w);
+            L.total_ctas += ((bN + g.V - 1) / g.V + segs - 1) / segs;
+        }
+        L.item_cta0[i + 1] = L.total_ctas;
+        L.harm0[i + 1] = L.harm0[i] + harm_blocks_for(pl, n[i]);
+        h.counts[(size_t)i * JERK_MAX_STAGES] = (double)bN * nt_item;
+        for (int si = 1; si < ns; ++si)
+            h.counts[(size_t)i * JERK_MAX_STAGES + si] = (double)nf_stage[si] * n_cells(bN, pl->prm.stages[si]);
+    }
+    ConvGroup end;
+    std::memset(&end, 0, sizeof(end));
+    end.cta0 = (int32_t)L.total_ctas;
+    h.work.push_back(end);
+    L.n_work = (int)h.work.size() - 1;
+    // capacity checks (the plan was sized for max_bins bins in total)
+    if (spec > pl->prm.max_bins || L.slot_base[count] > pl->slot_cap ||
+        2 * (L.total_ctas + (int64_t)ns * L.harm0[count]) > pl->stat_part_cap || L.total_ctas >= INT32_MAX)
+        return JERK_ENOMEM;
+    for (int si = 0; si < ns; ++si)
+        if (m[si] > n_cells((int64_t)pl->b * pl->prm.max_bins, pl->prm.stages[si]) + pl->max_batch)
+            return JERK_ENOMEM;
+    return JERK_OK;
+}
+
+void fill_items(const jerk_plan_s *pl, const BatchLayout &L, HostTables &h) {
+    for (size_t i = 0; i < L.n.size(); ++i) {
+        ItemDesc &it = h.items[i];
+        it.spec = pl->d_spec_norm + L.spec_off[i];
+        it.N = L.n[i];
+        it.bN = (int64_t)pl->b * L.n[i];
+        it.M1 = pl->d_M[0] + L.m_off[0][i];
+        it.slot_off = L.d_soff + i * pl->n_entries;
+        it.slot_len = L.d_slen + i * pl->n_entries;
+    }
+}
+
+// Cached tables: own device buffers, synchronous upload.
+jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n,
+                         const std::vector<int32_t> &zm, const std::vector<int32_t> &wm) {
+    HostTables h;
+    const jerk_status s = plan_tables(pl, L, n, zm, wm, h);
+    if (s != JERK_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_items, sizeof(ItemDesc) * h.items.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_work, sizeof(ConvGroup) * h.work.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_soff, sizeof(int64_t) * h.soff.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_slen, sizeof(int64_t) * h.slen.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_fund, sizeof(FundEntry) * h.fund.size());
+    if (e == cudaSuccess) e = cudaMalloc(&L.d_counts, sizeof(double) * h.counts.size());
+    if (e == cudaSuccess && !h.rows.empty()) e = cudaMalloc(&L.d_rows, sizeof(int32_t) * h.rows.size());
+    if (e == cudaSuccess && !h.tl.empty()) e = cudaMalloc(&L.d_tl, sizeof(int32_t) * h.tl.size());
+    if (e != cudaSuccess) return from_cuda(e);
+    fill_items(pl, L, h);
+    auto up = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    up(L.d_items, h.items.data(), sizeof(ItemDesc) * h.items.size());
+    up(L.d_work, h.work.data(), sizeof(ConvGroup) * h.work.size());
+    up(L.d_soff, h.soff.data(), sizeof(int64_t) * h.soff.size());
+    up(L.d_slen, h.slen.data(), sizeof(int64_t) * h.slen.size());
+    up(L.d_fund, h.fund.data(), sizeof(FundEntry) * h.fund.size());
+    up(L.d_counts, h.counts.data(), sizeof(double) * h.counts.size());
+    up(L.d_rows, h.rows.data(), sizeof(int32_t) * h.rows.size());
+    up(L.d_tl, h.tl.data(), sizeof(int32_t) * h.tl.size());
+    return from_cuda(e);
+}
+
+// Launch tables for a set of spectrum lengths (and sub-grids): reused from a
+// small LRU cache, built on first use (a host synchronisation).
+jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, const std::vector<int32_t> &zm,
+                          const std::vector<int32_t> &wm, cudaStream_t st) {
     for (BatchLayout *L : pl->layouts)
-        if (L->n == n) {
+        if (L->n == n && L->zmax == zm && L->wmax == wm) {
             L->last_use = ++pl->use_clock;
             pl->cur = L;
             return JERK_OK;
@@ -279,17 +459,19 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaSt
     if (pl->layouts.size() >= kMaxLayouts) {
         L = *std::min_element(pl->layouts.begin(), pl->layouts.end(),
                               [](const BatchLayout *x, const BatchLayout *y) { return x->last_use < y->last_use; });
+        if (pl->cur == L) pl->cur = nullptr;
         free_layout(*L);
     } else {
         L = new (std::nothrow) BatchLayout();
         if (!L) return JERK_ENOMEM;
         pl->layouts.push_back(L);
     }
-    const jerk_status s = build_layout(pl, *L, n);
+    const jerk_status s = build_layout(pl, *L, n, zm, wm);
     if (s != JERK_OK) {
+        free_layout(*L);
         pl->layouts.erase(std::find(pl->layouts.begin(), pl->layouts.end(), L));
-        delete L;
         if (pl->cur == L) pl->cur = nullptr;
+        delete L;
         return s;
     }
     L->last_use = ++pl->use_clock;
@@ -297,100 +479,80 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaSt
     return JERK_OK;
 }
 
-jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n) {
-    const int count = (int)n.size();
-    const int ns = pl->prm.n_stages;
-    L.n = n;
-    L.item_cta0.assign(count + 1, 0);
-    L.harm0.assign(count + 1, 0);
-    L.spec_off.assign(count, 0);
-    L.slot_base.assign(count + 1, 0);
-    for (int si = 0; si < ns; ++si) L.m_off[si].assign(count, 0);
-    std::vector<int64_t> soff((size_t)count * std::max(pl->n_entries, 1)), slen(soff.size());
-    std::vector<FundEntry> fund((size_t)count * std::max(pl->n_fund, 1));
-    std::vector<ConvGroup> work;
-    std::vector<double> counts((size_t)count * JERK_MAX_STAGES, 0.0);
-    int64_t spec = 0, m[JERK_MAX_STAGES] = {0, 0, 0, 0};
-    const int segs = conv_segs_per_cta(pl->log2L);
-    for (int i = 0; i < count; ++i) {
-        const int64_t bN = (int64_t)pl->b * n[i];
-        L.spec_off[i] = spec;
-        spec += n[i];
-        for (int si = 0; si < ns; ++si) {
-            L.m_off[si][i] = m[si];
-            m[si] += n_cells(bN, pl->prm.stages[si]);
+jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, cudaStream_t st) {
+    static const std::vector<int32_t> none;
+    return ensure_layout(pl, n, none, none, st);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Transient tables: built into the plan's preallocated buffers and uploaded by
+// one asynchronous copy from pinned staging on `st`.  Waits (on the host) only
+// for this plan's previous search, whose upload used the same staging.
+jerk_status transient_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, const std::vector<int32_t> &zm,
+                             const std::vector<int32_t> &wm, cudaStream_t st) {
+    TransientTables &tt = pl->tt;
+    if (!tt.d_buf) {
+        // capacity: max_batch items, each with every group, entry, fundamental and template
+        const size_t mb = (size_t)pl->max_batch;
+        tt.cap_work = (int64_t)(mb * pl->groups.size() + 1);
+        tt.cap_ent = (int64_t)(mb * std::max(pl->n_entries, 1));
+        tt.cap_fund = (int64_t)(mb * std::max(pl->n_fund, 1));
+        tt.cap_rows = (int64_t)(mb * pl->T);
+        tt.bytes = align256(sizeof(ItemDesc) * mb) + align256(sizeof(ConvGroup) * tt.cap_work) +
+                   2 * align256(sizeof(int64_t) * tt.cap_ent) + align256(sizeof(FundEntry) * tt.cap_fund) +
+                   align256(sizeof(double) * mb * JERK_MAX_STAGES) + 2 * align256(sizeof(int32_t) * tt.cap_rows);
+        cudaError_t e = cudaMalloc(&tt.d_buf, tt.bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&tt.h_stage, tt.bytes);
+        if (e != cudaSuccess) {
+            if (tt.d_buf) cudaFree(tt.d_buf);
+            tt = TransientTables();
+            return from_cuda(e);
         }
-        const int64_t used = item_rows(pl, n[i], L.slot_base[i], soff.data() + (size_t)i * pl->n_entries,
-                                       slen.data() + (size_t)i * pl->n_entries,
-                                       fund.data() + (size_t)i * pl->n_fund);
-        L.slot_base[i + 1] = L.slot_base[i] + used;
-        // conv work: this spectrum's (group, segment range) entries, item-major
-        for (const auto &g : pl->groups) {
-            ConvGroup w = g;
-            w.cta0 = (int32_t)L.total_ctas;
-            w.item = i;
-            work.push_back(w);
-            L.total_ctas += ((bN + g.V - 1) / g.V + segs - 1) / segs;
-        }
-        L.item_cta0[i + 1] = L.total_ctas;
-        L.harm0[i + 1] = L.harm0[i] + harm_blocks_for(pl, n[i]);
-        counts[(size_t)i * JERK_MAX_STAGES] = (double)bN * pl->T;
-        for (int si = 1; si < ns; ++si) {
-            int64_t nf = 0;
-            for (int f = 0; f < pl->n_fund; ++f)
-                if (pl->fund_top[f] >= si) ++nf;
-            counts[(size_t)i * JERK_MAX_STAGES + si] = (double)nf * n_cells(bN, pl->prm.stages[si]);
-        }
+        pl->bytes += (int64_t)tt.bytes;
     }
-    ConvGroup end;
-    std::memset(&end, 0, sizeof(end));
-    end.cta0 = (int32_t)L.total_ctas;
-    work.push_back(end);
-    L.n_work = (int)work.size() - 1;
-    // capacity checks (the plan was sized for max_bins bins in total)
-    if (spec > pl->prm.max_bins || L.slot_base[count] > pl->slot_cap ||
-        2 * (L.total_ctas + (int64_t)ns * L.harm0[count]) > pl->stat_part_cap) {
-        free_layout(L);
-        return JERK_ENOMEM;
+    BatchLayout &L = pl->transient_layout;
+    HostTables h;
+    const jerk_status s = plan_tables(pl, L, n, zm, wm, h);
+    if (s != JERK_OK) return s;
+    if ((int64_t)h.work.size() > tt.cap_work || (int64_t)h.rows.size() > tt.cap_rows) return JERK_ENOMEM;
+    // section offsets (capacity-sized, so the device pointers never move)
+    const size_t mb = (size_t)pl->max_batch;
+    char *d0 = (char *)tt.d_buf;
+    size_t o = 0;
+    const size_t o_items = o;  o += align256(sizeof(ItemDesc) * mb);
+    const size_t o_work = o;   o += align256(sizeof(ConvGroup) * tt.cap_work);
+    const size_t o_soff = o;   o += align256(sizeof(int64_t) * tt.cap_ent);
+    const size_t o_slen = o;   o += align256(sizeof(int64_t) * tt.cap_ent);
+    const size_t o_fund = o;   o += align256(sizeof(FundEntry) * tt.cap_fund);
+    const size_t o_counts = o; o += align256(sizeof(double) * mb * JERK_MAX_STAGES);
+    const size_t o_rows = o;   o += align256(sizeof(int32_t) * tt.cap_rows);
+    const size_t o_tl = o;
+    L.d_items = (ItemDesc *)(d0 + o_items);
+    L.d_work = (ConvGroup *)(d0 + o_work);
+    L.d_soff = (int64_t *)(d0 + o_soff);
+    L.d_slen = (int64_t *)(d0 + o_slen);
+    L.d_fund = (FundEntry *)(d0 + o_fund);
+    L.d_counts = (double *)(d0 + o_counts);
+    L.d_rows = h.rows.empty() ? nullptr : (int32_t *)(d0 + o_rows);
+    L.d_tl = h.tl.empty() ? nullptr : (int32_t *)(d0 + o_tl);
+    L.graph = nullptr;
+    fill_items(pl, L, h);
+    JCHECK(cudaEventSynchronize(pl->done));   // the previous upload has left the staging buffer
+    char *h0 = (char *)tt.h_stage;
+    std::memcpy(h0 + o_items, h.items.data(), sizeof(ItemDesc) * h.items.size());
+    std::memcpy(h0 + o_work, h.work.data(), sizeof(ConvGroup) * h.work.size());
+    std::memcpy(h0 + o_soff, h.soff.data(), sizeof(int64_t) * h.soff.size());
+    std::memcpy(h0 + o_slen, h.slen.data(), sizeof(int64_t) * h.slen.size());
+    std::memcpy(h0 + o_fund, h.fund.data(), sizeof(FundEntry) * h.fund.size());
+    std::memcpy(h0 + o_counts, h.counts.data(), sizeof(double) * h.counts.size());
+    if (!h.rows.empty()) {
+        std::memcpy(h0 + o_rows, h.rows.data(), sizeof(int32_t) * h.rows.size());
+        std::memcpy(h0 + o_tl, h.tl.data(), sizeof(int32_t) * h.tl.size());
     }
-    for (int si = 0; si < ns; ++si)
-        if (m[si] > n_cells((int64_t)pl->b * pl->prm.max_bins, pl->prm.stages[si]) + pl->max_batch) {
-            free_layout(L);
-            return JERK_ENOMEM;
-        }
-    std::vector<ItemDesc> items(count);
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_items, sizeof(ItemDesc) * count);
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_work, sizeof(ConvGroup) * work.size());
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_soff, sizeof(int64_t) * soff.size());
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_slen, sizeof(int64_t) * slen.size());
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_fund, sizeof(FundEntry) * fund.size());
-    if (e == cudaSuccess) e = cudaMalloc(&L.d_counts, sizeof(double) * counts.size());
-    if (e != cudaSuccess) {
-        free_layout(L);
-        return from_cuda(e);
-    }
-    for (int i = 0; i < count; ++i) {
-        items[i].spec = pl->d_spec_norm + L.spec_off[i];
-        items[i].N = n[i];
-        items[i].bN = (int64_t)pl->b * n[i];
-        items[i].M1 = pl->d_M[0] + L.m_off[0][i];
-        items[i].slot_off = L.d_soff + (size_t)i * pl->n_entries;
-        items[i].slot_len = L.d_slen + (size_t)i * pl->n_entries;
-    }
-    if (e == cudaSuccess) e = cudaMemcpy(L.d_items, items.data(), sizeof(ItemDesc) * count, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(L.d_work, work.data(), sizeof(ConvGroup) * work.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.d_soff, soff.data(), sizeof(int64_t) * soff.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(L.d_slen, slen.data(), sizeof(int64_t) * slen.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(L.d_fund, fund.data(), sizeof(FundEntry) * fund.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(L.d_counts, counts.data(), sizeof(double) * counts.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        free_layout(L);
-        return from_cuda(e);
-    }
+    const size_t used = h.rows.empty() ? o_rows : o_tl + sizeof(int32_t) * h.tl.size();
+    JCHECK(cudaMemcpyAsync(tt.d_buf, tt.h_stage, used, cudaMemcpyHostToDevice, st));
+    pl->cur = &L;
     return JERK_OK;
 }
 
@@ -422,7 +584,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
     std::memset(&a, 0, sizeof(a));
     a.items = L.d_items;
     a.bank = pl->d_bank;
-    a.order = pl->d_order;
+    a.order = L.d_tl ? L.d_tl : pl->d_order;
+    a.rows = L.d_rows;
     a.grp = L.d_work;
     a.n_work = L.n_work;
     a.T = pl->T;
@@ -445,7 +608,7 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
             std::memset(&h, 0, sizeof(h));
             h.slots = pl->d_slots;
             h.fund = L.d_fund + (size_t)i * pl->n_fund;
-            h.n_fund = pl->n_fund;
+            h.n_fund = L.n_fund[i];
             h.n_stages = ns;
             for (int si = 0; si < ns; ++si) {
                 h.stages[si] = pl->prm.stages[si];
@@ -453,7 +616,7 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
                 h.M[si] = pl->d_M[si] + L.m_off[si][i];
             }
             h.stat_part = partH + 2 * ns * L.harm0[i];
-            h.f_chunk = pl->n_fund;
+            h.f_chunk = L.n_fund[i];
             const int64_t nthreads = (h.n_cells[1] + 3) / 4;   // 4 cells per thread
             JCHECK(launch_harmonic(h, nthreads, 1, sigma, st));
         }
@@ -508,6 +671,138 @@ jerk_status finish_search(jerk_plan_s *pl, cudaStream_t st, int count, bool prof
     return JERK_OK;
 }
 
+// ---- plan construction ------------------------------------------------------
+
+// Grid values, segment length, template groups and harmonic-row structure of
+// pl->prm (host only).
+jerk_status plan_structure(jerk_plan_s *pl) {
+    const jerk_params *params = &pl->prm;
+    pl->b = params->numbetween;
+    pl->nz = 2 * params->zmax / params->dz + 1;
+    pl->nw = 2 * params->wmax / params->dw + 1;
+    pl->T = pl->nz * pl->nw;
+    pl->zt.resize(pl->T);
+    pl->wt.resize(pl->T);
+    pl->mt.resize(pl->T);
+    pl->M = 0;
+    for (int j = 0; j < pl->nw; ++j)
+        for (int i = 0; i < pl->nz; ++i) {
+            const int t = j * pl->nz + i;
+            pl->zt[t] = -params->zmax + i * params->dz;
+            pl->wt[t] = -params->wmax + j * params->dw;
+            pl->mt[t] = halfwidth(pl->zt[t], pl->wt[t], params->pad_bins);
+            pl->M = std::max(pl->M, pl->mt[t]);
+        }
+    pl->K = 2 * pl->b * pl->M + 1;
+    if (params->seg_len) {
+        pl->L = params->seg_len;
+    } else {
+        double best = 1e300;
+        for (int lg = 10; lg <= 13; ++lg) {
+            const int L = 1 << lg, V = L - pl->K + 1;
+            if (V < L / 4) continue;
+            const double cost = (fft_passes(lg) + 1.0) * L / V;
+            if (cost < best - 1e-9) {
+                best = cost;
+                pl->L = L;
+            }
+        }
+        if (best >= 1e300) return JERK_EINVAL;
+    }
+    pl->log2L = 0;
+    while ((1 << pl->log2L) < pl->L) ++pl->log2L;
+    pl->V = pl->L - pl->K + 1;
+    if (pl->V < 64) return JERK_EINVAL;
+    build_row_structure(pl);
+    build_groups(pl, tpg_for(pl, nseg_for(pl, params->max_bins), pl->T));
+    return JERK_OK;
+}
+
+// Device memory of a plan: with own_bank, the template bank and per-template
+// tables (a new BankShare); always the workspace a search writes, sized for
+// any set of at most max_batch spectra totalling at most max_bins bins.
+jerk_status plan_memory(jerk_plan_s *pl, bool own_bank) {
+    const jerk_params *params = &pl->prm;
+    const int64_t N = params->max_bins, bN = (int64_t)pl->b * N;
+    const int ns = params->n_stages;
+    // (rows, CTAs and harmonic blocks grow with n; each extra spectrum adds rounding)
+    pl->slot_cap = item_rows(pl, N, params->zmax, params->wmax, 0, nullptr, nullptr, nullptr, nullptr, nullptr) +
+                   (int64_t)pl->max_batch * 32 * std::max(1, pl->n_fund * JERK_MAX_HARMONIC);
+    const int64_t conv_blocks = ctas_for(pl, N) + (int64_t)pl->max_batch * (int64_t)pl->groups.size();
+    const int64_t harm_blocks = harm_blocks_for(pl, N) + pl->max_batch;
+    pl->stat_part_cap = 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
+
+    // does it fit?
+    size_t free_b = 0, total_b = 0;
+    JCHECK(cudaMemGetInfo(&free_b, &total_b));
+    int64_t need = 2 * N * 8 + pl->slot_cap * 4 + pl->stat_part_cap * 8 +
+                   params->max_candidates * (int64_t)sizeof(DevCand);
+    if (own_bank) need += (int64_t)pl->T * pl->L * 8 + (int64_t)pl->T * 40;
+    for (int si = 0; si < ns; ++si) need += (n_cells(bN, params->stages[si]) + pl->max_batch) * 8;
+    if ((double)need > 0.97 * (double)free_b) return JERK_ENOMEM;
+
+    cudaError_t e = cudaSuccess;
+#define TRY(x) \
+    if (e == cudaSuccess) e = (x)
+    if (own_bank) {
+        BankShare *sh = new (std::nothrow) BankShare();
+        if (!sh) return JERK_ENOMEM;
+        sh->device = pl->device;
+        pl->share.reset(sh);
+        TRY(dalloc(&sh->bytes, &sh->d_bank, (size_t)pl->T * pl->L));
+        TRY(dalloc(&sh->bytes, &sh->d_zt, (size_t)pl->T));
+        TRY(dalloc(&sh->bytes, &sh->d_order, (size_t)pl->T));
+        TRY(dalloc(&sh->bytes, &sh->d_wt, (size_t)pl->T));
+        TRY(dalloc(&sh->bytes, &sh->d_slot_beg, (size_t)pl->T + 1));
+        TRY(dalloc(&sh->bytes, &sh->d_slot_h, (size_t)pl->n_entries));
+        TRY(dalloc(&sh->bytes, &sh->d_gl, 64));
+        TRY(cudaMemcpy(sh->d_zt, pl->zt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+        TRY(cudaMemcpy(sh->d_order, pl->order.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+        TRY(cudaMemcpy(sh->d_wt, pl->wt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
+        TRY(cudaMemcpy(sh->d_slot_beg, pl->h_slot_beg.data(), sizeof(int32_t) * (pl->T + 1),
+                       cudaMemcpyHostToDevice));
+        if (pl->n_entries)
+            TRY(cudaMemcpy(sh->d_slot_h, pl->h_slot_h.data(), sizeof(int32_t) * pl->n_entries,
+                           cudaMemcpyHostToDevice));
+        if (e == cudaSuccess) {
+            std::vector<double> x, w;
+            gauss_legendre(64, x, w);
+            std::vector<double2> gl(64);
+            for (int i = 0; i < 64; ++i) gl[i] = make_double2(x[i], w[i]);
+            e = cudaMemcpy(sh->d_gl, gl.data(), sizeof(double2) * 64, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) {
+        const BankShare *sh = pl->share.get();
+        pl->d_bank = sh->d_bank;
+        pl->d_zt = sh->d_zt;
+        pl->d_wt = sh->d_wt;
+        pl->d_order = sh->d_order;
+        pl->d_slot_beg = sh->d_slot_beg;
+        pl->d_slot_h = sh->d_slot_h;
+        pl->d_gl = sh->d_gl;
+        pl->n_gl = 64;
+    }
+    TRY(dalloc(&pl->bytes, &pl->d_spec_in, (size_t)N));
+    TRY(dalloc(&pl->bytes, &pl->d_spec_norm, (size_t)N));
+    for (int si = 0; si < ns; ++si)
+        TRY(dalloc(&pl->bytes, &pl->d_M[si], (size_t)(n_cells(bN, params->stages[si]) + pl->max_batch)));
+    TRY(dalloc(&pl->bytes, &pl->d_slots, (size_t)pl->slot_cap));
+    TRY(dalloc(&pl->bytes, &pl->d_stat_part, (size_t)pl->stat_part_cap));
+    TRY(dalloc(&pl->bytes, &pl->d_stats, (size_t)2 * JERK_MAX_STAGES * pl->max_batch));
+    TRY(dalloc(&pl->bytes, &pl->d_thresh, (size_t)JERK_MAX_STAGES));
+    TRY(dalloc(&pl->bytes, &pl->d_theta, (size_t)JERK_MAX_STAGES * pl->max_batch));
+    TRY(dalloc(&pl->bytes, &pl->d_cand, (size_t)params->max_candidates));
+    TRY(dalloc(&pl->bytes, &pl->d_count, 1));
+    TRY(dalloc(&pl->bytes, &pl->d_err, 1));
+    TRY(cudaMemset(pl->d_err, 0, sizeof(int)));
+    TRY(cudaMallocHost((void **)&pl->h_cand, sizeof(DevCand) * (size_t)params->max_candidates));
+    TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
+    TRY(cudaMemcpy(pl->d_thresh, params->thresh, sizeof(float) * JERK_MAX_STAGES, cudaMemcpyHostToDevice));
+#undef TRY
+    return from_cuda(e);
+}
+
 }  // namespace
 
 extern "C" {
@@ -539,117 +834,70 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     pl->prm = *params;
     pl->device = device;
     pl->max_batch = std::max(1, params->max_batch);
-    pl->b = params->numbetween;
-    pl->nz = 2 * params->zmax / params->dz + 1;
-    pl->nw = 2 * params->wmax / params->dw + 1;
-    pl->T = pl->nz * pl->nw;
-    pl->zt.resize(pl->T);
-    pl->wt.resize(pl->T);
-    pl->mt.resize(pl->T);
-    pl->M = 0;
-    for (int j = 0; j < pl->nw; ++j)
-        for (int i = 0; i < pl->nz; ++i) {
-            const int t = j * pl->nz + i;
-            pl->zt[t] = -params->zmax + i * params->dz;
-            pl->wt[t] = -params->wmax + j * params->dw;
-            pl->mt[t] = halfwidth(pl->zt[t], pl->wt[t], params->pad_bins);
-            pl->M = std::max(pl->M, pl->mt[t]);
-        }
-    pl->K = 2 * pl->b * pl->M + 1;
-    if (params->seg_len) {
-        pl->L = params->seg_len;
-    } else {
-        double best = 1e300;
-        for (int lg = 10; lg <= 13; ++lg) {
-            const int L = 1 << lg, V = L - pl->K + 1;
-            if (V < L / 4) continue;
-            const double cost = (fft_passes(lg) + 1.0) * L / V;
-            if (cost < best - 1e-9) {
-                best = cost;
-                pl->L = L;
-            }
-        }
-        if (best >= 1e300) {
-            delete pl;
-            return JERK_EINVAL;
-        }
-    }
-    pl->log2L = 0;
-    while ((1 << pl->log2L) < pl->L) ++pl->log2L;
-    pl->V = pl->L - pl->K + 1;
-    if (pl->V < 64) {
-        delete pl;
-        return JERK_EINVAL;
-    }
-
-    const int64_t N = params->max_bins, bN = (int64_t)pl->b * N;
-    const int ns = params->n_stages;
-    build_row_structure(pl);
-    build_groups(pl, tpg_for(pl, nseg_for(pl, N), pl->T));
-    // capacities for any set of at most max_batch spectra totalling at most N bins
-    // (rows, CTAs and harmonic blocks grow with n; each extra spectrum adds rounding)
-    pl->slot_cap = item_rows(pl, N, 0, nullptr, nullptr, nullptr) +
-                   (int64_t)pl->max_batch * 32 * std::max(1, pl->n_fund * JERK_MAX_HARMONIC);
-    const int64_t conv_blocks = ctas_for(pl, N) + (int64_t)pl->max_batch * (int64_t)pl->groups.size();
-    const int64_t harm_blocks = harm_blocks_for(pl, N) + pl->max_batch;
-    pl->stat_part_cap = 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
-
-    // does it fit?
-    size_t free_b = 0, total_b = 0;
-    JCHECK(cudaMemGetInfo(&free_b, &total_b));
-    int64_t need = (int64_t)pl->T * pl->L * 8 + 2 * N * 8 + pl->slot_cap * 4 + pl->stat_part_cap * 8 +
-                   params->max_candidates * (int64_t)sizeof(DevCand) + (int64_t)pl->T * 40;
-    for (int si = 0; si < ns; ++si) need += (n_cells(bN, params->stages[si]) + pl->max_batch) * 8;
-    if ((double)need > 0.97 * (double)free_b) {
-        delete pl;
-        return JERK_ENOMEM;
-    }
-
-    cudaError_t e = cudaSuccess;
-#define TRY(x) \
-    if (e == cudaSuccess) e = (x)
-    TRY(dalloc(pl, &pl->d_bank, (size_t)pl->T * pl->L));
-    TRY(dalloc(pl, &pl->d_spec_in, (size_t)N));
-    TRY(dalloc(pl, &pl->d_spec_norm, (size_t)N));
-    for (int si = 0; si < ns; ++si)
-        TRY(dalloc(pl, &pl->d_M[si], (size_t)(n_cells(bN, params->stages[si]) + pl->max_batch)));
-    TRY(dalloc(pl, &pl->d_slots, (size_t)pl->slot_cap));
-    TRY(dalloc(pl, &pl->d_zt, (size_t)pl->T));
-    TRY(dalloc(pl, &pl->d_order, (size_t)pl->T));
-    TRY(dalloc(pl, &pl->d_wt, (size_t)pl->T));
-    TRY(dalloc(pl, &pl->d_slot_beg, (size_t)pl->T + 1));
-    TRY(dalloc(pl, &pl->d_slot_h, (size_t)pl->n_entries));
-    TRY(dalloc(pl, &pl->d_stat_part, (size_t)pl->stat_part_cap));
-    TRY(dalloc(pl, &pl->d_stats, (size_t)2 * JERK_MAX_STAGES * pl->max_batch));
-    TRY(dalloc(pl, &pl->d_thresh, (size_t)JERK_MAX_STAGES));
-    TRY(dalloc(pl, &pl->d_theta, (size_t)JERK_MAX_STAGES * pl->max_batch));
-    TRY(dalloc(pl, &pl->d_cand, (size_t)params->max_candidates));
-    TRY(dalloc(pl, &pl->d_count, 1));
-    TRY(dalloc(pl, &pl->d_err, 1));
-    TRY(cudaMemset(pl->d_err, 0, sizeof(int)));
-    TRY(dalloc(pl, &pl->d_gl, 64));
-    TRY(cudaMallocHost((void **)&pl->h_cand, sizeof(DevCand) * (size_t)params->max_candidates));
-    TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
-    TRY(cudaMemcpy(pl->d_zt, pl->zt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(pl->d_order, pl->order.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(pl->d_wt, pl->wt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(pl->d_slot_beg, pl->h_slot_beg.data(), sizeof(int32_t) * (pl->T + 1), cudaMemcpyHostToDevice));
-    if (pl->n_entries)
-        TRY(cudaMemcpy(pl->d_slot_h, pl->h_slot_h.data(), sizeof(int32_t) * pl->n_entries, cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy(pl->d_thresh, params->thresh, sizeof(float) * JERK_MAX_STAGES, cudaMemcpyHostToDevice));
-    if (e == cudaSuccess) {
-        std::vector<double> x, w;
-        gauss_legendre(64, x, w);
-        std::vector<double2> gl(64);
-        for (int i = 0; i < 64; ++i) gl[i] = make_double2(x[i], w[i]);
-        e = cudaMemcpy(pl->d_gl, gl.data(), sizeof(double2) * 64, cudaMemcpyHostToDevice);
-        pl->n_gl = 64;
-    }
-#undef TRY
-    if (e != cudaSuccess) {
+    v = plan_structure(pl);
+    if (v == JERK_OK) v = plan_memory(pl, true);
+    if (v != JERK_OK) {
         release(pl);
         delete pl;
-        return from_cuda(e);
+        return v;
+    }
+    *out = pl;
+    return JERK_OK;
+}
+
+jerk_status jerk_plan_share(jerk_plan parent, const jerk_params *params, jerk_plan *out) {
+    if (!out) return JERK_EINVAL;
+    *out = nullptr;
+    if (!parent) return JERK_EINVAL;
+    jerk_status v = validate(params);
+    if (v != JERK_OK) return v;
+    const jerk_params &q = parent->prm;
+    // the bank-defining parameters must be the parent's
+    if (params->zmax != q.zmax || params->dz != q.dz || params->wmax != q.wmax || params->dw != q.dw ||
+        params->numbetween != q.numbetween || params->pad_bins != q.pad_bins || params->n_stages != q.n_stages ||
+        params->precision != q.precision || (params->seg_len != 0 && params->seg_len != parent->L))
+        return JERK_EINVAL;
+    for (int i = 0; i < q.n_stages; ++i)
+        if (params->stages[i] != q.stages[i]) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(parent->device));
+
+    jerk_plan_s *pl = new (std::nothrow) jerk_plan_s();
+    if (!pl) return JERK_ENOMEM;
+    pl->prm = *params;
+    pl->prm.seg_len = parent->L;
+    pl->device = parent->device;
+    pl->max_batch = std::max(1, params->max_batch);
+    // the parent's structure: its groups fix the tap offset baked into every bank row
+    pl->b = parent->b;
+    pl->nz = parent->nz;
+    pl->nw = parent->nw;
+    pl->T = parent->T;
+    pl->M = parent->M;
+    pl->K = parent->K;
+    pl->L = parent->L;
+    pl->log2L = parent->log2L;
+    pl->V = parent->V;
+    pl->zt = parent->zt;
+    pl->wt = parent->wt;
+    pl->mt = parent->mt;
+    pl->order = parent->order;
+    pl->row_of = parent->row_of;
+    pl->groups = parent->groups;
+    pl->n_entries = parent->n_entries;
+    pl->n_fund = parent->n_fund;
+    pl->ent_f = parent->ent_f;
+    pl->ent_h = parent->ent_h;
+    pl->fund_t = parent->fund_t;
+    pl->fund_top = parent->fund_top;
+    pl->fh_entry = parent->fh_entry;
+    pl->h_slot_beg = parent->h_slot_beg;
+    pl->h_slot_h = parent->h_slot_h;
+    pl->share = parent->share;
+    v = plan_memory(pl, false);
+    if (v != JERK_OK) {
+        release(pl);
+        delete pl;
+        return v;
     }
     *out = pl;
     return JERK_OK;
@@ -677,6 +925,7 @@ jerk_status jerk_plan_info(jerk_plan pl, jerk_info *info) {
     info->max_bins = pl->prm.max_bins;
     info->slot_floats = pl->slot_cap;
     info->workspace_bytes = pl->bytes;
+    info->bank_bytes = pl->share ? pl->share->bytes : 0;
     info->transforms = transforms_for(pl, pl->prm.max_bins);
     info->n_groups = (int32_t)pl->groups.size();
     info->reserved = 0;
@@ -746,7 +995,7 @@ jerk_status jerk_templates(jerk_plan pl, void *stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
     JCHECK(cudaEventRecord(pl->done, st));
-    pl->templates_ready = true;
+    pl->share->ready = true;
     return JERK_OK;
 }
 
@@ -762,7 +1011,7 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
                        void *stream) {
     if (!pl || !d_spec || !d_out || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
     if (t0 < 0 || nt < 1 || (int64_t)t0 + nt > pl->T) return JERK_EINVAL;
-    if (!pl->templates_ready) return JERK_ESTATE;
+    if (!bank_ready(pl)) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
     JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
@@ -794,7 +1043,7 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
 
 jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *stream) {
     if (!pl || !d_spec || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
-    if (!pl->templates_ready) return JERK_ESTATE;
+    if (!bank_ready(pl)) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
     JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
@@ -806,21 +1055,39 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     return finish_search(pl, st, 1, pl->profile);
 }
 
-jerk_status jerk_search_batch(jerk_plan pl, const void *const *d_specs, const int64_t *n, int32_t count,
-                              int32_t flags, void *stream) {
+jerk_status jerk_search_batch_grid(jerk_plan pl, const void *const *d_specs, const int64_t *n, const int32_t *zmax,
+                                   const int32_t *wmax, int32_t count, int32_t flags, void *stream) {
     if (!pl || !d_specs || !n || count < 1 || count > pl->max_batch) return JERK_EINVAL;
-    if (flags & ~JERK_BATCH_GRAPH) return JERK_EINVAL;
+    if (flags & ~(JERK_BATCH_GRAPH | JERK_BATCH_TRANSIENT)) return JERK_EINVAL;
+    if ((flags & JERK_BATCH_GRAPH) && (flags & JERK_BATCH_TRANSIENT)) return JERK_EINVAL;
+    if ((zmax == nullptr) != (wmax == nullptr)) return JERK_EINVAL;
     int64_t total = 0;
     for (int i = 0; i < count; ++i) {
         if (!d_specs[i] || n[i] < 1) return JERK_EINVAL;
         total += n[i];
     }
     if (total > pl->prm.max_bins) return JERK_EINVAL;
-    if (!pl->templates_ready) return JERK_ESTATE;
+    // sub-grids: on the bank's grid and inside it; all-whole-bank batches use the plain tables
+    std::vector<int32_t> zm, wm;
+    if (zmax) {
+        bool whole = true;
+        for (int i = 0; i < count; ++i) {
+            if (zmax[i] < 0 || zmax[i] > pl->prm.zmax || zmax[i] % pl->prm.dz) return JERK_EINVAL;
+            if (wmax[i] < 0 || wmax[i] > pl->prm.wmax || wmax[i] % pl->prm.dw) return JERK_EINVAL;
+            whole = whole && zmax[i] == pl->prm.zmax && wmax[i] == pl->prm.wmax;
+        }
+        if (!whole) {
+            zm.assign(zmax, zmax + count);
+            wm.assign(wmax, wmax + count);
+        }
+    }
+    if (!bank_ready(pl)) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
     JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
-    jerk_status s = ensure_layout(pl, std::vector<int64_t>(n, n + count), st);
+    const std::vector<int64_t> nv(n, n + count);
+    jerk_status s = (flags & JERK_BATCH_TRANSIENT) ? transient_layout(pl, nv, zm, wm, st)
+                                                   : ensure_layout(pl, nv, zm, wm, st);
     if (s != JERK_OK) return s;
     if (!(flags & JERK_BATCH_GRAPH)) {
         std::vector<const float2 *> in(count);
@@ -862,9 +1129,14 @@ jerk_status jerk_search_batch(jerk_plan pl, const void *const *d_specs, const in
     return finish_search(pl, st, count, false);
 }
 
+jerk_status jerk_search_batch(jerk_plan pl, const void *const *d_specs, const int64_t *n, int32_t count,
+                              int32_t flags, void *stream) {
+    return jerk_search_batch_grid(pl, d_specs, n, nullptr, nullptr, count, flags, stream);
+}
+
 jerk_status jerk_search_host(jerk_plan pl, const void *h_spec, int64_t n, void *stream) {
     if (!pl || !h_spec || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
-    if (!pl->templates_ready) return JERK_ESTATE;
+    if (!bank_ready(pl)) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     cudaStream_t st = (cudaStream_t)stream;
     JCHECK(cudaStreamWaitEvent(st, pl->done, 0));

@@ -22,7 +22,8 @@ THRESH_ABS, THRESH_SIGMA = 0, 1
 EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_host", "jerk_search_batch",
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
-           "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row")
+           "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
+           "jerk_search_batch_grid", "jerk_plan_share")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -51,7 +52,8 @@ class Info(ctypes.Structure):
                 ("seg_len", ctypes.c_int32), ("seg_valid", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("max_bins", ctypes.c_int64), ("slot_floats", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64), ("transforms", ctypes.c_int64),
-                ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32), ("d_bank", ctypes.c_void_p)]
+                ("n_groups", ctypes.c_int32), ("reserved", ctypes.c_int32), ("d_bank", ctypes.c_void_p),
+                ("bank_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -87,6 +89,9 @@ def lib() -> ctypes.CDLL:
             "jerk_phase_times": ([vp, ctypes.POINTER(ctypes.c_float), i32], st),
             "jerk_peaks_noalloc": ([vp, i64, ctypes.c_float, i32, i32, i32, i32, i32, vp, i64, vp, vp], st),
             "jerk_template_row": ([vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+            "jerk_search_batch_grid": ([vp, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                        ctypes.POINTER(i32), i32, i32, vp], st),
+            "jerk_plan_share": ([vp, ctypes.POINTER(Params), ctypes.POINTER(vp)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -137,6 +142,7 @@ CANDIDATE_DTYPE = np.dtype([("p", "<i8"), ("r", "<f8"), ("t", "<i4"), ("z_idx", 
                             ("stage", "<i4"), ("z", "<f4"), ("w", "<f4"), ("power", "<f4"),
                             ("item", "<i4")])
 BATCH_GRAPH = 1
+BATCH_TRANSIENT = 2
 
 
 def peaks_noalloc(d_maxproj: int, n_cells: int, theta: float, stage: int, zmax: int, dz: int, wmax: int,
@@ -151,10 +157,17 @@ def peaks_noalloc(d_maxproj: int, n_cells: int, theta: float, stage: int, zmax: 
 class Plan:
     """One search configuration on one device; owns the template bank."""
 
-    def __init__(self, params: Params, device: int = 0, build_templates: bool = True, stream=None):
+    def __init__(self, params: Params, device: int = 0, build_templates: bool = True, stream=None,
+                 share_with: "Plan | None" = None):
         self.params = params
         h = ctypes.c_void_p()
-        _check(lib().jerk_plan_create(ctypes.byref(params), device, ctypes.byref(h)), "jerk_plan_create")
+        if share_with is not None:
+            # the bank of `share_with`, a workspace of this plan's own
+            _check(lib().jerk_plan_share(share_with._h, ctypes.byref(params), ctypes.byref(h)), "jerk_plan_share")
+            device = share_with.device
+            build_templates = False
+        else:
+            _check(lib().jerk_plan_create(ctypes.byref(params), device, ctypes.byref(h)), "jerk_plan_create")
         self._h = h
         self.device = device
         self.info = Info()
@@ -190,14 +203,35 @@ class Plan:
         _check(lib().jerk_search(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(),
                                  _stream_handle(stream)), "jerk_search")
 
-    def search_batch(self, specs, graph: bool = False, stream=None):
-        """Enqueue one batched search of several complex64 CUDA tensors."""
+    def share(self, params: Params) -> "Plan":
+        """A new plan over this plan's template bank with its own workspace
+        (jerk_plan_share)."""
+        return Plan(params, share_with=self)
+
+    def search_batch(self, specs, graph: bool = False, stream=None, zmax=None, wmax=None,
+                     transient: bool = False):
+        """Enqueue one batched search of several complex64 CUDA tensors;
+        with zmax / wmax (one value per spectrum) each spectrum is searched
+        over its own sub-grid of the bank (jerk_search_batch_grid)."""
         n = len(specs)
         ptrs = (ctypes.c_void_p * n)(*[ctypes.c_void_p(s.data_ptr()) for s in specs])
         lens = (ctypes.c_int64 * n)(*[s.numel() for s in specs])
         self._batch_ref = specs
-        _check(lib().jerk_search_batch(self._h, ptrs, lens, n, BATCH_GRAPH if graph else 0,
-                                       _stream_handle(stream)), "jerk_search_batch")
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_TRANSIENT if transient else 0)
+        if zmax is None and wmax is None and not transient:
+            _check(lib().jerk_search_batch(self._h, ptrs, lens, n, flags, _stream_handle(stream)),
+                   "jerk_search_batch")
+            return
+        zp = wp = None
+        if zmax is not None or wmax is not None:
+            zmax = [int(self.params.zmax)] * n if zmax is None else list(zmax)
+            wmax = [int(self.params.wmax)] * n if wmax is None else list(wmax)
+            if len(zmax) != n or len(wmax) != n:
+                raise ValueError("one zmax and one wmax per spectrum")
+            zp = (ctypes.c_int32 * n)(*zmax)
+            wp = (ctypes.c_int32 * n)(*wmax)
+        _check(lib().jerk_search_batch_grid(self._h, ptrs, lens, zp, wp, n, flags, _stream_handle(stream)),
+               "jerk_search_batch_grid")
 
     def search_host(self, spec: np.ndarray, stream=None):
         """Enqueue a search of a host complex64 array (copied by the library)."""
@@ -207,10 +241,17 @@ class Plan:
                                       _stream_handle(stream)), "jerk_search_host")
 
     def candidates(self, cap: int | None = None):
-        """Synchronise and return the candidates as a list of tuples
-        (stage, p, t, power) sorted by (stage, p), plus the records."""
+        """Synchronise and return the candidate records (Candidate) sorted by
+        (item, stage, p).  Without `cap` the count is read first and the
+        buffer sized to it."""
         if cap is None:
-            cap = int(self.params.max_candidates)
+            n = ctypes.c_int64()
+            code = lib().jerk_candidates(self._h, None, 0, ctypes.byref(n))
+            if code not in (JERK_OK, JERK_EOVERFLOW):
+                _check(code, "jerk_candidates")
+            if n.value > int(self.params.max_candidates):
+                raise JerkError(JERK_EOVERFLOW, "jerk_candidates (%d found)" % n.value)
+            cap = n.value
         buf = (Candidate * max(cap, 1))()
         n = ctypes.c_int64()
         code = lib().jerk_candidates(self._h, buf, cap, ctypes.byref(n))
