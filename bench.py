@@ -57,6 +57,8 @@ def args_():
     ap.add_argument("--autotune", action="store_true", help="pick the segment length by timing (cached)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seg-len", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0, choices=(0, 1, 2),
+                    help="filter arithmetic: 0 FP32, 1 BF16 tensor-core DFT blocks, 2 FP16 tensor-core DFT blocks")
     ap.add_argument("--bins", type=int, default=1 << 22,
                     help="spectrum length of the paper-scale bank (smaller for profiling)")
     return ap.parse_args()
@@ -197,6 +199,47 @@ def oracle_sample(wl, spec, budget_s=12.0, stride=16, cells=65536):
             "(t = 0, %d, ...) over cells [%d, %d) of the %d-bin workload; template "
             "build and normalisation not counted" % (len(used), stride, p0, p0 + cells, wl.n_bins))
     return done / corr_s, done, oracle.threads(), desc
+
+
+def tc_accuracy(wl, spec, plan, x, fp32_cands, tc_cands, cells=65536):
+    """Error of the reduced-precision filter against the FP64 oracle on a
+    sample: three runs of 64 consecutive templates (z from -128 to -2 + 126 at
+    w = -wmax, 0, +wmax) over `cells` cells in the middle of the spectrum
+    (the plane rows come from jerk_plane, the reference from the oracle's
+    direct correlation).  Also the candidate agreement with the FP32 filter on
+    the whole workload."""
+    import numpy as np
+    import torch
+
+    import oracle
+    op = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages)
+    zt, wt = oracle.grid(op)
+    nz, nw = 2 * wl.zmax // wl.dz + 1, 2 * wl.wmax // wl.dw + 1
+    p0 = wl.n_bins - cells // 2
+    Fn = oracle.normalise(spec, op.norm_block)
+    i0 = max(0, nz // 2 - 64)
+    errs, refmax, sq, cnt = [], 0.0, 0.0, 0
+    for j in (0, nw // 2, nw - 1):
+        t0 = j * nz + i0
+        nt = min(64, nz - i0)
+        out = torch.empty((nt, 2 * wl.n_bins), dtype=torch.float32, device=x.device)
+        plan.plane(x, t0, nt, out)
+        got = out[:, p0:p0 + cells].cpu().numpy().astype(np.float64)
+        for k in range(nt):
+            t = t0 + k
+            c = oracle.taps(int(zt[t]), int(wt[t]), op.numbetween, op.pad_bins)
+            o = oracle.correlate(Fn, c, op.numbetween, p0, cells)
+            ref = o.real * o.real + o.imag * o.imag
+            d = np.abs(got[k] - ref)
+            errs.append(float(d.max()))
+            sq += float((d * d).sum())
+            cnt += d.size
+            refmax = max(refmax, float(ref.max()))
+    a, b = set(fp32_cands), set(tc_cands)
+    return {"vs": "FP64 oracle, direct correlation", "templates": 3 * 64, "cells": cells,
+            "max_err_rel_plane_max": max(errs) / refmax, "rms_err_rel_plane_max": (sq / cnt) ** 0.5 / refmax,
+            "candidates_fp32": len(a), "candidates": len(b), "common": len(a & b),
+            "only_fp32": len(a - b), "only_this": len(b - a)}
 
 
 def reference_arm(a):
@@ -413,7 +456,7 @@ def main():
     spec = synth.spectrum(wl.n_bins, wl.seed + 1000 * rank, wl.signals) if rank else wl.make()
     p = pkg.make_params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages,
                         thresh=SIGMA_T[:len(wl.stages)], thresh_mode=pkg.THRESH_SIGMA,
-                        seg_len=a.seg_len, max_bins=wl.n_bins, max_candidates=1 << 20)
+                        seg_len=a.seg_len, max_bins=wl.n_bins, max_candidates=1 << 20, precision=a.precision)
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     plan = pkg.Plan(p, device=local, stream=stream)
@@ -486,6 +529,36 @@ def main():
     traffic = recorded_traffic(L)
     peaks, peaks_src = peaks_file()
 
+    roof = {"bound": "alu", "kernel": "conv_kernel (fused FFT-multiply-IFFT-power)",
+            "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+            "frac": achieved / peak_alu, "traffic": traffic,
+            "flops_per_cell": conv_flops_per_cell(L, V),
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+    accuracy = None
+    if a.precision:
+        # tensor pipe: two 64-point DFT blocks per point and transform, 8 flops per
+        # point per unit of radix (complex products as real block products)
+        tflops_cell = 8.0 * (64 + 64) * L / V
+        t_achieved = tflops_cell * cells / (conv_ms / 1e3) / 1e12
+        t_peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        roof = {"bound": "tensor", "kernel": "conv_tc_kernel (DFT blocks on tcgen05, %s operands)"
+                                             % ("BF16" if a.precision == 1 else "FP16"),
+                "achieved": t_achieved, "peak": t_peak, "unit": "TFLOP/s", "frac": t_achieved / t_peak,
+                "traffic": None, "flops_per_cell": tflops_cell,
+                "peak_source": "%s dense bf16 (sustained), FP16 at the same rate" % peaks_src,
+                "alu_view": {"achieved": achieved, "peak": peak_alu, "frac": achieved / peak_alu,
+                             "note": "FP32-equivalent transform flops (5 L log2 L + 6 L + 3 V per segment)"}}
+        if rank == 0 and world == 1:
+            p32 = pkg.make_params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages,
+                                  thresh=SIGMA_T[:len(wl.stages)], thresh_mode=pkg.THRESH_SIGMA,
+                                  max_bins=wl.n_bins, max_candidates=1 << 20)
+            with pkg.Plan(p32, device=local) as plan32:
+                plan32.search(d_spec)
+                c32 = [(int(c.stage), int(c.p), int(c.t)) for c in plan32.candidates()]
+            plan.search(d_spec)
+            ctc = [(int(c.stage), int(c.p), int(c.t)) for c in plan.candidates()]
+            accuracy = tc_accuracy(wl, spec, plan, d_spec, c32, ctc)
+
     if rank == 0:
         cpu = None
         if world == 1 and not a.no_cpu_baseline:
@@ -496,7 +569,8 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": ("f32", "bf16", "f16")[a.precision],
+            "data": "synthetic",
             "config": {"workload": wl.name, "n_bins": wl.n_bins, "templates": plan.info.n_templates,
                        "cells_per_step": cells, "stages": list(wl.stages), "thresh_mode": "sigma",
                        "thresh_T": list(SIGMA_T[:len(wl.stages)]), "seg_len": L, "seg_valid": V,
@@ -507,11 +581,7 @@ def main():
             "phase_ms": phase_mean,
             "candidates": ncand,
             "templates_s": round(t_templates, 3),
-            "roofline": {"bound": "alu", "kernel": "conv_kernel (fused FFT-multiply-IFFT-power)",
-                         "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                         "frac": achieved / peak_alu, "traffic": traffic,
-                         "flops_per_cell": conv_flops_per_cell(L, V),
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
+            "roofline": roof,
             "plain_form_ceiling": {"value": peaks["hbm_gbs"] * 1e9 / 8.0, "unit": UNIT,
                                    "note": "unfused plane write + read, 8 B/cell at %s HBM %.1f GB/s"
                                            % (peaks_src, peaks["hbm_gbs"])},
@@ -521,6 +591,8 @@ def main():
             "gpu_launches": 5 * a.steps,
             "clocks": clk,
         }
+        if accuracy is not None:
+            line["accuracy"] = accuracy
         print(json.dumps(line))
     plan.close()
     if dist:

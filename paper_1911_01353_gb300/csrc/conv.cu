@@ -21,6 +21,7 @@
 // another agent is the mbarrier of the bulk copy; it is bounded (about one
 // second of %globaltimer) and on expiry the CTA records an error flag that
 // the host reports as JERK_ETIMEOUT.
+#include "device_sync.cuh"
 #include "fft.cuh"
 #include "jerk_internal.h"
 
@@ -30,51 +31,6 @@ namespace jerk {
 // (16-byte reads of the h = 1 row), at most 2-way conflicts for the
 // digit-reversed writes and 3-way for the h = 2 reads
 __device__ __forceinline__ int swzf(int a) { return a ^ (((a >> 5) & 7) << 2); }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-// one elected thread: expect `bytes` and start the bulk global -> shared copy
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// wait for phase `parity` of `bar`, giving up after ~1 s
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
-    return true;
-}
 
 template <int LOG2L>
 struct ConvCfg {
@@ -103,20 +59,6 @@ __device__ __forceinline__ float tree16(const float (&x)[16]) {
     a[0] = a[0] + a[1];
     a[2] = a[2] + a[3];
     return a[0] + a[2];
-}
-
-// OR of `pred` over the `n` threads of named barrier `id` (also a barrier)
-__device__ __forceinline__ bool named_any(int id, int n, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(n)
-        : "memory");
-    return r != 0;
 }
 
 template <int LOG2L, int SIGN>

@@ -1,0 +1,544 @@
+// Reduced-precision form of the fused overlap-and-save filter (Sec. 2,
+// Fig. 1): the inverse transform of every (segment, template) product runs on
+// the 5th-generation tensor cores as 64-point DFT blocks recast as dense
+// products, with BF16 or FP16 operands and FP32 accumulation in tensor memory.
+//
+// Segment length L = 4096 = 64 x 64 (Cooley-Tukey, k = k1 + 64 k2 and
+// n = 64 n1 + n2):
+//   y[64 n1 + n2] = sum_k1 F[n1][k1] w^{k1 n2} sum_k2 Z[k1 + 64 k2] F[k2][n2],
+// with F[a][b] = exp(+2 pi i a b / 64), w = exp(+2 pi i / L) and Z the
+// product of the segment spectrum and the template spectrum (1/L folded into
+// the bank).  One CTA holds two segments, so each step is a 128 x 128 x 128
+// real product (complex values in real block form, [re | im]):
+//   step 1: D1 = A1 B      A1[(seg, k1)][(re/im, k2)] = Z          (K-major)
+//   twiddle U'[k1][n2] = D1 w^{k1 n2}   (FP32, in registers)
+//   step 3: D3 = A3 B      A3[(seg, n2)][(re/im, k1)] = U'         (MN-major)
+// where B is the real block form of F (the same matrix for both steps, F is
+// symmetric).  D1 and D3 sit in tensor memory; every thread reads one row
+// (tcgen05.ld), so the power |y|^2, the running max over the template group,
+// the statistics and the harmonic rows are computed as in the FP32 kernel.
+//
+// Scaling: each segment spectrum is divided by max|X| * max|C| over the bank,
+// so |Z| <= 1 and the FP16 operands of both steps stay in range (|U'| <= 64,
+// |y| <= 4096 in FP32); powers are multiplied back before any use.
+//
+// One elected thread issues the MMAs (tcgen05.mma, operands in shared memory
+// through matrix descriptors, no swizzle) and commits them to an mbarrier.
+// Every wait on another agent (template bulk copies, MMA completion) is
+// bounded (~1 s of %globaltimer); on expiry the CTA sets the plan's error flag
+// (JERK_ETIMEOUT on the host), stops, drains its bulk copies and frees its
+// tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "device_sync.cuh"
+#include "fft.cuh"
+#include "jerk_internal.h"
+
+namespace jerk {
+namespace {
+
+constexpr int L = 4096, LOG2L = 12, NT = 256, SEGS = 2, THREADS = 512;
+constexpr int WPAD = L + L / 16;                          // forward-transform work, per segment
+constexpr uint32_t LBO = 128;                             // operand core-matrix stride along K (bytes)
+constexpr uint32_t SBO = 2048;                            // ... along M / N (16 cores of 128 B along K)
+constexpr int OPB = 128 * 128 * 2;                        // one 16-bit 128 x 128 operand
+constexpr int OFF_A1 = 2 * L * 8;                         // after the two-deep template ring
+constexpr int OFF_A3 = OFF_A1 + OPB;
+constexpr int OFF_B = OFF_A3 + OPB;                       // B, then the twiddle table (one bulk copy)
+constexpr int OFF_TW = OFF_B + OPB;                       // float2 [n2][k1] = w^{k1 n2}
+constexpr int OFF_AMX = OFF_TW + 64 * 64 * 8;             // uint16 [SEGS][L]: argmax offset in the group
+constexpr int SMEM = OFF_AMX + SEGS * L * 2;              // 212 992 bytes
+constexpr uint32_t TMEM_COLS = 256;                       // D1: columns 0..127, D3: 128..255
+static_assert(SEGS * WPAD * 8 <= OFF_A3, "forward-transform work must fit below A3");
+
+template <int PREC>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if constexpr (PREC == 1) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+__device__ __forceinline__ void sts128(uint32_t addr, const uint32_t (&v)[8], int o) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v[o]), "r"(v[o + 1]), "r"(v[o + 2]),
+                 "r"(v[o + 3])
+                 : "memory");
+}
+
+// shared-memory matrix descriptor: no swizzle, fixed version bits 46-48 = 0b001
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32, A/B BF16 (PREC 1) or FP16 (PREC 2),
+// A K-major or MN-major, B K-major, M = N = 128
+template <int PREC, bool A_MN>
+__device__ __forceinline__ uint32_t idesc() {
+    const uint32_t t = PREC == 1 ? 1u : 0u;
+    return (1u << 4) | (t << 7) | (t << 10) | ((A_MN ? 1u : 0u) << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+// D[128 x 128] (tensor memory) = A[128 x 128] B[128 x 128], 8 steps of K = 16
+template <int PREC, bool A_MN>
+__device__ __forceinline__ void mma_tile(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr) {
+    const uint32_t id = idesc<PREC, A_MN>();
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        const uint64_t ad = sdesc(a_addr + s * 2 * LBO), bd = sdesc(b_addr + s * 2 * LBO);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(ad), "l"(bd), "r"(id), "r"((uint32_t)(s > 0))
+            : "memory");
+    }
+}
+
+// one K = 16 step s (0..7) of that product
+template <int PREC, bool A_MN>
+__device__ __forceinline__ void mma_step(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr, int s) {
+    const uint64_t ad = sdesc(a_addr + s * 2 * LBO), bd = sdesc(b_addr + s * 2 * LBO);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc<PREC, A_MN>()), "r"((uint32_t)(s > 0))
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's tensor-memory lane; the wait
+// carries the registers so that no use is scheduled before it
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&x)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(r[i]);
+}
+
+template <bool ROWS>
+__device__ __forceinline__ int tc_bank_row(const ConvArgs &a, int k) {
+    if constexpr (ROWS) return __ldg(a.rows + k);
+    return k;
+}
+
+template <int PREC, int MODE, bool STATS, bool ROWS>
+__global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    float2 *ring = reinterpret_cast<float2 *>(sm);
+    uint16_t *amx_s = reinterpret_cast<uint16_t *>(sm + OFF_AMX);
+    __shared__ __align__(8) uint64_t full[2];                 // template bulk copy landed
+    __shared__ __align__(8) uint64_t mbar1, mbar3, cbar;      // step 1 / step 3 done; constants landed
+    __shared__ int issued[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int xmax_bits[SEGS];
+    __shared__ double red[2][THREADS / 32];
+    __shared__ double dacc[STATS ? 2 : 1][STATS ? THREADS : 1];
+
+    const int tid = threadIdx.x;
+    const int half = tid / NT, j = tid % NT;                  // forward-transform mapping
+    const int warp = tid >> 5, lane = tid & 31;
+    const int quarter = warp & 3, gcol = warp >> 2;           // tensor-memory lane quarter, column group
+    const int row = 32 * quarter + lane;                      // operand / accumulator row: (seg, r)
+    const int seg = row >> 6, r = row & 63;
+
+    // (spectrum, template group) entry of this CTA: binary search of the CTA prefix
+    int lo = 0, hi = a.n_work - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((int)blockIdx.x >= __ldg(&a.grp[mid].cta0)) lo = mid; else hi = mid - 1;
+    }
+    const ItemDesc *itm = a.items + __ldg(&a.grp[lo].item);
+    const int V = __ldg(&a.grp[lo].V), bM = __ldg(&a.grp[lo].bM);
+    const int tb = __ldg(&a.grp[lo].tb), te = __ldg(&a.grp[lo].te);
+    const int s_base = ((int)blockIdx.x - __ldg(&a.grp[lo].cta0)) * SEGS;
+    const int64_t bN = itm->bN;
+
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&mbar1, 1);
+        mbar_init(&mbar3, 1);
+        mbar_init(&cbar, 1);
+        issued[0] = issued[1] = 0;
+        xmax_bits[0] = xmax_bits[1] = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t tlane = (uint32_t)(32 * quarter) << 16;
+    // B and the twiddle table: one bulk copy (not aliased by the transform work)
+    if (tid == 0) bulk_load(sm + OFF_B, a.tc_const, (uint32_t)(OPB + 64 * 64 * 8), &cbar);
+
+    // ---- 1. forward FFT of each spread segment (FP32) -------------------------
+    {
+        float2 v[16];
+        float2 *work = reinterpret_cast<float2 *>(sm) + half * WPAD;
+        const SyncNamed bar_half{1 + half, NT};
+        FftTw<LOG2L, -1> twf;
+        twf.init(j);
+        const float2 *spec = itm->spec;
+        const int64_t N = itm->N;
+        const int64_t in0 = (int64_t)(s_base + half) * V - bM;   // first spread sample (even)
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const int64_t q = in0 + j + NT * m;
+            float2 x = make_float2(0.f, 0.f);
+            if (((q & 1) == 0) && q >= 0 && (q >> 1) < N) x = spec[q >> 1];
+            v[m] = x;
+        }
+        fft_pass0<LOG2L, -1>(v, twf);
+        fft_store0<LOG2L>(v, work, j);
+        fft_rest<LOG2L, -1>(v, work, j, twf, bar_half);
+        const int rv = fft_rev<LOG2L>(j);
+        bar_half();
+#pragma unroll
+        for (int m = 0; m < 16; ++m) work[rv + NT * m] = v[m];   // natural order
+    }
+    __syncthreads();
+    // this thread's spectrum values in the tensor-core mapping: X[seg][r + 64 (16 gcol + i)]
+    float2 xr[16];
+    {
+        const float2 *ws = reinterpret_cast<const float2 *>(sm) + seg * WPAD;
+        float m = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            xr[i] = ws[r + 64 * (16 * gcol + i)];
+            m = fmaxf(m, fmaxf(fabsf(xr[i].x), fabsf(xr[i].y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) atomicMax(&xmax_bits[seg], __float_as_int(m));   // non-negative: int order = float order
+    }
+    __syncthreads();                                          // the work buffers are free from here
+    if (tid == 0)
+        for (int b = 0; b < 2 && tb + b < te; ++b) {
+            issued[b] = 1;
+            bulk_load(ring + b * L, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + b) * L, (uint32_t)(L * sizeof(float2)),
+                      &full[b]);
+        }
+    float psc;                                                // power = |y|^2 * psc
+    {
+        const float xm = __int_as_float(xmax_bits[seg]);
+        const float cm = __ldg(a.tc_cmax);
+        const float sc = (xm > 0.f && cm > 0.f) ? 1.0f / (xm * cm) : 1.0f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) xr[i] = make_float2(xr[i].x * sc, xr[i].y * sc);
+        psc = 1.0f / (sc * sc);
+    }
+
+    // cells of this thread: n = 64 (16 gcol + i) + r of segment seg
+    const int seg0 = (s_base + seg) * V;
+    unsigned vmask = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const int n = 64 * (16 * gcol + i) + r;
+        if (n < V && seg0 + n < bN) vmask |= 1u << i;
+    }
+    float mx[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) mx[i] = -1.0f;
+    if constexpr (STATS) {
+        dacc[0][tid] = 0.0;
+        dacc[1][tid] = 0.0;
+    }
+    float c1 = 0.f, c2 = 0.f;
+    const uint32_t a1_row = smem_u32(sm + OFF_A1) + (row >> 3) * SBO + (row & 7) * 16;
+    const uint32_t a3_col = smem_u32(sm + OFF_A3) + (r >> 3) * LBO + (r & 7) * 16 + (8 * seg + 2 * gcol) * SBO;
+    const float2 *twt = reinterpret_cast<const float2 *>(sm + OFF_TW);
+
+    // ---- the three thread phases of one template --------------------------------
+    // The issuing thread (tid 0) interleaves the eight K steps of the product it
+    // launches with its own share of a phase: tcgen05.mma blocks while the
+    // tensor core's queue is full, so one step per slice of work keeps its warp
+    // from stalling for the whole product.
+    const uint32_t sA1 = smem_u32(sm + OFF_A1), sA3 = smem_u32(sm + OFF_A3), sB = smem_u32(sm + OFF_B);
+    // A: Z = X C (scaled) -> A1 (K-major), from ring buffer `b`; issues step 3
+    // of the previous template when `issue3`
+    auto phase_a = [&](int b, bool issue3) {
+        const float2 *C = ring + b * L;
+        uint32_t pr[8], pi[8];
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+            const float2 z0 = cmul(xr[i], C[r + 64 * (16 * gcol + i)]);
+            const float2 z1 = cmul(xr[i + 1], C[r + 64 * (16 * gcol + i + 1)]);
+            pr[i >> 1] = pack2<PREC>(z0.x, z1.x);
+            pi[i >> 1] = pack2<PREC>(z0.y, z1.y);
+            if (issue3) mma_step<PREC, true>(tmem + 128, sA3, sB, i >> 1);
+        }
+        if (issue3) mma_commit(&mbar3);
+        sts128(a1_row + (2 * gcol) * LBO, pr, 0);
+        sts128(a1_row + (2 * gcol + 1) * LBO, pr, 4);
+        sts128(a1_row + (8 + 2 * gcol) * LBO, pi, 0);
+        sts128(a1_row + (9 + 2 * gcol) * LBO, pi, 4);
+    };
+    // C: D1 -> twiddle -> A3 (MN-major)
+    auto phase_c = [&]() {
+        float ur[16], ui[16];
+        tmem_ld16(tmem + tlane + 16 * gcol, ur);
+        tmem_ld16(tmem + tlane + 64 + 16 * gcol, ui);
+        uint32_t pr[8], pi[8];
+#pragma unroll
+        for (int i = 0; i < 16; i += 2) {
+            const float2 u0 = cmul(make_float2(ur[i], ui[i]), twt[(16 * gcol + i) * 64 + r]);
+            const float2 u1 = cmul(make_float2(ur[i + 1], ui[i + 1]), twt[(16 * gcol + i + 1) * 64 + r]);
+            pr[i >> 1] = pack2<PREC>(u0.x, u1.x);
+            pi[i >> 1] = pack2<PREC>(u0.y, u1.y);
+        }
+        sts128(a3_col, pr, 0);
+        sts128(a3_col + SBO, pr, 4);
+        sts128(a3_col + 8 * LBO, pi, 0);
+        sts128(a3_col + 8 * LBO + SBO, pi, 4);
+    };
+    // E: D3 -> power, running max, statistics, harmonic rows (search) or plane
+    // rows; issues step 1 of the next template when `issue1`.  The running max
+    // and the statistics use |y|^2 before the segment's power scale psc (a
+    // monotone factor), applied when they leave the CTA.
+    auto phase_e = [&](int k, int it, bool issue1) {
+        float yr[16], yi[16];
+        tmem_ld16(tmem + tlane + 128 + 16 * gcol, yr);
+        tmem_ld16(tmem + tlane + 192 + 16 * gcol, yi);
+        float P[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) P[i] = fmaf(yr[i], yr[i], yi[i] * yi[i]);
+        const int t = __ldg(a.order + k);
+        if constexpr (MODE == 0) {
+            float s1 = 0.f, s2 = 0.f;
+            const bool all = vmask == 0xFFFFu;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                // cells outside the segment's valid range count as 0 (never read back)
+                const float pm = (all || ((vmask >> i) & 1u)) ? P[i] : 0.f;
+                const bool up = pm > mx[i];
+                mx[i] = up ? pm : mx[i];
+                if (up) amx_s[seg * L + 64 * (16 * gcol + i) + r] = (uint16_t)it;
+                s1 += pm;
+                s2 = fmaf(pm, pm, s2);
+                if (issue1 && (i & 1)) mma_step<PREC, false>(tmem, sA1, sB, i >> 1);
+            }
+            if (issue1) mma_commit(&mbar1);
+            if constexpr (STATS) {
+                c1 += s1;
+                c2 += s2;
+                if ((it & 31) == 31) {
+                    dacc[0][tid] += (double)c1 * (double)psc;
+                    dacc[1][tid] += (double)c2 * ((double)psc * (double)psc);
+                    c1 = c2 = 0.f;
+                }
+            }
+            // harmonic rows: cell q = seg0 + 64 (16 gcol + i) + r is harmonic h of
+            // fundamental cell q / h when h | q; quotient and remainder are stepped
+            // by 64 per i, so only one division per entry
+            const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
+            for (int e = e0; e < e1; ++e) {
+                const int h = __ldg(a.slot_h + e);
+                float *dst = a.slots + __ldg(itm->slot_off + e);
+                const int len = (int)__ldg(itm->slot_len + e);
+                const int q0 = seg0 + 64 * 16 * gcol + r;
+                int quo = q0 / h, rem = q0 - quo * h;
+                const int dq = 64 / h, dr = 64 - dq * h;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    if (((vmask >> i) & 1u) && rem == 0 && quo < len) dst[quo] = P[i] * psc;
+                    quo += dq;
+                    rem += dr;
+                    if (rem >= h) {
+                        rem -= h;
+                        quo += 1;
+                    }
+                }
+            }
+        } else {
+            if (issue1) {
+#pragma unroll
+                for (int s8 = 0; s8 < 8; ++s8) mma_step<PREC, false>(tmem, sA1, sB, s8);
+                mma_commit(&mbar1);
+            }
+            if (t >= a.t0 && t < a.t0 + a.nt) {
+                float *prow = a.plane + (int64_t)(t - a.t0) * bN + seg0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if ((vmask >> i) & 1u) prow[64 * (16 * gcol + i) + r] = P[i] * psc;
+            }
+        }
+    };
+
+    // ---- software pipeline over the group's templates ------------------------------
+    // iteration it:  C(it) | A(it+1) with step 3 of it issued || E(it) with step 1
+    // of it+1 issued, so each product runs while the threads work on the other.
+    const int nt = te - tb;
+    bool fail = !mbar_wait_bounded(&cbar, 0);
+    fail = __any_sync(0xffffffffu, fail);
+    if (nt > 0) {
+        if (!fail) fail = !mbar_wait_bounded(&full[0], 0);
+        fail = __any_sync(0xffffffffu, fail);
+        if (!fail) phase_a(0, false);
+        fence_async_smem();
+        fail = __syncthreads_or(fail);
+        if (!fail && tid == 0) {
+            tc_fence_after();
+            mma_tile<PREC, false>(tmem, sA1, sB);
+            mma_commit(&mbar1);
+        }
+        if (!fail && tid == 32 && nt > 2) {                    // buffer 0 is read: template 2 next
+            issued[0] += 1;
+            bulk_load(ring, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + 2) * L, (uint32_t)(L * sizeof(float2)),
+                      &full[0]);
+        }
+    }
+    for (int it = 0; !fail && it < nt; ++it) {
+        // C(it): step 1 of template it has landed in D1
+        fail = !mbar_wait_bounded(&mbar1, (uint32_t)it & 1u);
+        fail = __any_sync(0xffffffffu, fail);
+        tc_fence_after();
+        if (!fail) phase_c();
+        tc_fence_before();
+        fence_async_smem();
+        if (__syncthreads_or(fail)) {
+            fail = true;
+            break;
+        }
+        const bool more = it + 1 < nt;
+        if (more) {
+            // A(it + 1) while step 3 of template it runs
+            const int b = (it + 1) & 1;
+            if (tid == 0) tc_fence_after();
+            fail = !mbar_wait_bounded(&full[b], (uint32_t)((it + 1) >> 1) & 1u);
+            fail = __any_sync(0xffffffffu, fail);
+            if (!fail) phase_a(b, tid == 0);
+            fence_async_smem();
+            if (__syncthreads_or(fail)) {
+                fail = true;
+                break;
+            }
+            if (tid == 32 && it + 3 < nt) {                   // buffer b is read: template it + 3 next
+                issued[b] += 1;
+                bulk_load(ring + b * L, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + it + 3) * L,
+                          (uint32_t)(L * sizeof(float2)), &full[b]);
+            }
+            if (tid == 0) tc_fence_after();
+        } else if (tid == 0) {
+            tc_fence_after();
+            mma_tile<PREC, true>(tmem + 128, sA3, sB);
+            mma_commit(&mbar3);
+        }
+        // E(it): step 3 of template it has landed in D3; step 1 of it + 1 runs meanwhile
+        fail = !mbar_wait_bounded(&mbar3, (uint32_t)it & 1u);
+        fail = __any_sync(0xffffffffu, fail);
+        tc_fence_after();
+        if (!fail) phase_e(tb + it, it, more && tid == 0);
+        tc_fence_before();
+    }
+    fail = __syncthreads_or(fail);
+
+    // ---- epilogue -----------------------------------------------------------------
+    if (fail && tid == 0) atomicExch(a.err, 1);
+    if constexpr (MODE == 0) {
+        if (!fail && tb < te) {
+            unsigned long long *M1 = itm->M1;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                if ((vmask >> i) & 1u) {
+                    const int n = 64 * (16 * gcol + i) + r;
+                    const int tw = __ldg(a.order + tb + amx_s[seg * L + n]);
+                    const unsigned long long packed = ((unsigned long long)__float_as_uint(mx[i] * psc) << 32) |
+                                                      (unsigned long long)(0xFFFFFFFFu - (unsigned)tw);
+                    atomicMax(M1 + seg0 + n, packed);
+                }
+            }
+        }
+        if constexpr (STATS) {
+            double d1 = dacc[0][tid] + (double)c1 * (double)psc;
+            double d2 = dacc[1][tid] + (double)c2 * ((double)psc * (double)psc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+                d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            }
+            if (lane == 0) {
+                red[0][warp] = d1;
+                red[1][warp] = d2;
+            }
+            __syncthreads();
+            if (tid == 0) {
+                double s1 = 0.0, s2 = 0.0;
+                for (int w = 0; w < THREADS / 32; ++w) {
+                    s1 += red[0][w];
+                    s2 += red[1][w];
+                }
+                a.stat_part[2 * (int64_t)blockIdx.x] = s1;
+                a.stat_part[2 * (int64_t)blockIdx.x + 1] = s2;
+            }
+        }
+    }
+    if (tid == 0) {
+        // never leave with a bulk copy still writing into this CTA's shared memory
+        for (int b = 0; b < 2; ++b)
+            if (issued[b] > 0) mbar_wait_bounded(&full[b], (uint32_t)(issued[b] - 1) & 1u);
+        mbar_wait_bounded(&cbar, 0);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+template <int PREC, int MODE, bool STATS, bool ROWS>
+cudaError_t launch_tc_one(const ConvArgs &a, int n_ctas, cudaStream_t st) {
+    auto k = conv_tc_kernel<PREC, MODE, STATS, ROWS>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    k<<<n_ctas, THREADS, SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+cudaError_t launch_tc_prec(int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st) {
+    if (mode == 1) return launch_tc_one<PREC, 1, false, false>(a, n_ctas, st);
+    if (a.rows) return stats ? launch_tc_one<PREC, 0, true, true>(a, n_ctas, st)
+                             : launch_tc_one<PREC, 0, false, true>(a, n_ctas, st);
+    return stats ? launch_tc_one<PREC, 0, true, false>(a, n_ctas, st)
+                 : launch_tc_one<PREC, 0, false, false>(a, n_ctas, st);
+}
+
+}  // namespace
+
+cudaError_t launch_conv_tc(int precision, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st) {
+    if (!a.tc_const || !a.tc_cmax) return cudaErrorInvalidValue;
+    if (precision == 1) return launch_tc_prec<1>(mode, stats, a, n_ctas, st);
+    if (precision == 2) return launch_tc_prec<2>(mode, stats, a, n_ctas, st);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace jerk

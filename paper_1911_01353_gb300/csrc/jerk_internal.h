@@ -64,6 +64,9 @@ struct ConvArgs {
     int *err;                // set to 1 when a bounded device wait expires
     // plane mode
     float *plane;            // [nt][bN]
+    // reduced-precision (tensor-core) filter
+    const void *tc_const;    // 16-bit B operand (32 KB) then the twiddle table (float2 [64][64])
+    const float *tc_cmax;    // max over the bank of max(|Re C|, |Im C|)
 };
 
 struct HarmArgs {
@@ -97,6 +100,8 @@ cudaError_t launch_template_fft(const double2 *taps, const int32_t *shift, const
                                 int L, const double2 *tw, float2 *bank, cudaStream_t st);
 cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st);
 cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
+cudaError_t launch_conv_tc(int precision, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
+cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, cudaStream_t st);
 int conv_segs_per_cta(int log2L);
 cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats,
                             cudaStream_t st);
@@ -142,6 +147,7 @@ struct BankShare {
     int32_t *d_zt = nullptr, *d_wt = nullptr, *d_order = nullptr;
     int32_t *d_slot_beg = nullptr, *d_slot_h = nullptr;
     double2 *d_gl = nullptr;
+    float *d_cmax = nullptr;          // max(|Re|, |Im|) over the bank (set by jerk_templates)
     int64_t bytes = 0;
     std::atomic<bool> ready{false};   // jerk_templates has filled d_bank
     ~BankShare();
@@ -176,6 +182,8 @@ struct jerk_plan_s {
     std::vector<int32_t> row_of;       // t -> processing index
     std::vector<jerk::ConvGroup> groups;
     int32_t *d_order = nullptr;
+    void *d_tc = nullptr;              // tensor-core filter constants (precision 1, 2)
+    float *d_cmax = nullptr;
 
     int32_t *d_slot_beg = nullptr, *d_slot_h = nullptr;
     int n_entries = 0, n_fund = 0;

@@ -9,6 +9,9 @@
 #include <new>
 #include <vector>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "jerk_internal.h"
 
 using namespace jerk;
@@ -24,6 +27,7 @@ BankShare::~BankShare() {
     cudaFree(d_slot_beg);
     cudaFree(d_slot_h);
     cudaFree(d_gl);
+    cudaFree(d_cmax);
     if (had) cudaSetDevice(cur);
 }
 
@@ -233,7 +237,8 @@ jerk_status validate(const jerk_params *p) {
     for (int i = 0; i < p->n_stages; ++i)
         if (!std::isfinite(p->thresh[i])) return JERK_EINVAL;
     if (p->norm_block < 0 || p->norm_block > 4096) return JERK_EINVAL;
-    if (p->precision != 0) return JERK_EINVAL;
+    if (p->precision < 0 || p->precision > 2) return JERK_EINVAL;
+    if (p->precision != 0 && p->seg_len != 0 && p->seg_len != 4096) return JERK_EINVAL;   // 64 x 64 DFT blocks
     if (p->max_bins < 1 || p->max_bins > ((int64_t)1 << 29)) return JERK_EINVAL;
     if (p->max_candidates < 1 || p->max_candidates > ((int64_t)1 << 26)) return JERK_EINVAL;
     if (p->max_batch < 0 || p->max_batch > 4096) return JERK_EINVAL;
@@ -291,6 +296,7 @@ void release(jerk_plan_s *pl) {
     cudaFree(pl->d_cand);
     cudaFree(pl->d_count);
     cudaFree(pl->d_err);
+    cudaFree(pl->d_tc);
     if (pl->h_cand) cudaFreeHost(pl->h_cand);
     if (pl->done) cudaEventDestroy(pl->done);
     for (auto &e : pl->ev)
@@ -596,7 +602,10 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
     a.slots = pl->d_slots;
     a.stat_part = pl->d_stat_part;
     a.err = pl->d_err;
-    JCHECK(launch_conv(pl->log2L, 0, sigma, a, (int)L.total_ctas, st));
+    a.tc_const = pl->d_tc;
+    a.tc_cmax = pl->d_cmax;
+    JCHECK(pl->prm.precision ? launch_conv_tc(pl->prm.precision, 0, sigma, a, (int)L.total_ctas, st)
+                             : launch_conv(pl->log2L, 0, sigma, a, (int)L.total_ctas, st));
     JCHECK(mark(pl, 2, st, capturing));
 
     // harmonic sums for stages > 1, per spectrum
@@ -673,6 +682,46 @@ jerk_status finish_search(jerk_plan_s *pl, cudaStream_t st, int count, bool prof
 
 // ---- plan construction ------------------------------------------------------
 
+// Constants of the tensor-core filter (L = 4096 = 64 x 64): the real block
+// form of F[a][b] = exp(+2 pi i a b / 64),
+//   B[kk][c] = [[Re F, Im F], [-Im F, Re F]]  (kk: re | im of the input index,
+//                                               c: re | im of the output index),
+// as a 16-bit (BF16 for precision 1, FP16 for 2) K-major 128 x 128 operand in
+// 8 x 8 core matrices (128 B apart along K, 2048 B along N), followed by the
+// twiddle table tw[n2][k1] = exp(+2 pi i k1 n2 / 4096) as float2.  FP64
+// arithmetic, rounded once.
+std::vector<unsigned char> tc_constants(int precision) {
+    const double two_pi = 6.283185307179586476925286766559;
+    std::vector<unsigned char> out(128 * 128 * 2 + 64 * 64 * 8, 0);
+    for (int kk = 0; kk < 128; ++kk)
+        for (int c = 0; c < 128; ++c) {
+            const int a = kk & 63, bcol = c & 63;
+            const double ang = two_pi * (double)((a * bcol) % 64) / 64.0;
+            const double re = std::cos(ang), im = std::sin(ang);
+            double v;
+            if (kk < 64) v = c < 64 ? re : im;
+            else v = c < 64 ? -im : re;
+            uint16_t bits;
+            if (precision == 1) {
+                const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
+                std::memcpy(&bits, &h, 2);
+            } else {
+                const __half h = __float2half_rn((float)v);
+                std::memcpy(&bits, &h, 2);
+            }
+            const size_t off = (size_t)(c >> 3) * 2048 + (size_t)(kk >> 3) * 128 + (size_t)(c & 7) * 16 + (size_t)(kk & 7) * 2;
+            std::memcpy(out.data() + off, &bits, 2);
+        }
+    float *tw = reinterpret_cast<float *>(out.data() + 128 * 128 * 2);
+    for (int n2 = 0; n2 < 64; ++n2)
+        for (int k1 = 0; k1 < 64; ++k1) {
+            const double ang = two_pi * (double)(k1 * n2) / 4096.0;
+            tw[2 * (n2 * 64 + k1)] = (float)std::cos(ang);
+            tw[2 * (n2 * 64 + k1) + 1] = (float)std::sin(ang);
+        }
+    return out;
+}
+
 // Grid values, segment length, template groups and harmonic-row structure of
 // pl->prm (host only).
 jerk_status plan_structure(jerk_plan_s *pl) {
@@ -694,7 +743,9 @@ jerk_status plan_structure(jerk_plan_s *pl) {
             pl->M = std::max(pl->M, pl->mt[t]);
         }
     pl->K = 2 * pl->b * pl->M + 1;
-    if (params->seg_len) {
+    if (params->precision != 0) {
+        pl->L = 4096;                          // the tensor-core filter is built for 64 x 64 DFT blocks
+    } else if (params->seg_len) {
         pl->L = params->seg_len;
     } else {
         double best = 1e300;
@@ -756,6 +807,7 @@ jerk_status plan_memory(jerk_plan_s *pl, bool own_bank) {
         TRY(dalloc(&sh->bytes, &sh->d_slot_beg, (size_t)pl->T + 1));
         TRY(dalloc(&sh->bytes, &sh->d_slot_h, (size_t)pl->n_entries));
         TRY(dalloc(&sh->bytes, &sh->d_gl, 64));
+        TRY(dalloc(&sh->bytes, &sh->d_cmax, 1));
         TRY(cudaMemcpy(sh->d_zt, pl->zt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
         TRY(cudaMemcpy(sh->d_order, pl->order.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
         TRY(cudaMemcpy(sh->d_wt, pl->wt.data(), sizeof(int32_t) * pl->T, cudaMemcpyHostToDevice));
@@ -781,7 +833,14 @@ jerk_status plan_memory(jerk_plan_s *pl, bool own_bank) {
         pl->d_slot_beg = sh->d_slot_beg;
         pl->d_slot_h = sh->d_slot_h;
         pl->d_gl = sh->d_gl;
+        pl->d_cmax = sh->d_cmax;
         pl->n_gl = 64;
+    }
+    if (params->precision != 0 && e == cudaSuccess) {
+        const std::vector<unsigned char> c = tc_constants(params->precision);
+        TRY(cudaMalloc(&pl->d_tc, c.size()));
+        if (e == cudaSuccess) pl->bytes += (int64_t)c.size();
+        TRY(cudaMemcpy(pl->d_tc, c.data(), c.size(), cudaMemcpyHostToDevice));
     }
     TRY(dalloc(&pl->bytes, &pl->d_spec_in, (size_t)N));
     TRY(dalloc(&pl->bytes, &pl->d_spec_norm, (size_t)N));
@@ -987,6 +1046,7 @@ jerk_status jerk_templates(jerk_plan pl, void *stream) {
             e = launch_template_fft(taps, d_shift + k0, d_klen + k0, nt, pl->K, pl->L, tw,
                                     pl->d_bank + (size_t)k0 * pl->L, st);
     }
+    if (e == cudaSuccess) e = launch_bank_maxabs(pl->d_bank, (int64_t)pl->T * pl->L, pl->d_cmax, st);
     cudaFreeAsync(taps, st);
     if (tw) cudaFreeAsync(tw, st);
     if (d_shift) cudaFreeAsync(d_shift, st);
@@ -1036,7 +1096,10 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
     a.plane = d_out;
     a.err = pl->d_err;
     a.slot_beg = pl->d_slot_beg;
-    JCHECK(launch_conv(pl->log2L, 1, false, a, (int)pl->cur->total_ctas, st));
+    a.tc_const = pl->d_tc;
+    a.tc_cmax = pl->d_cmax;
+    JCHECK(pl->prm.precision ? launch_conv_tc(pl->prm.precision, 1, false, a, (int)pl->cur->total_ctas, st)
+                             : launch_conv(pl->log2L, 1, false, a, (int)pl->cur->total_ctas, st));
     JCHECK(cudaEventRecord(pl->done, st));
     return JERK_OK;
 }

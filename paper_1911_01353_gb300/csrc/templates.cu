@@ -168,6 +168,25 @@ __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int3
         dst[f] = make_float2((float)(buf[f].x * inv), (float)(buf[f].y * inv));
 }
 
+// out = max over the bank of max(|Re|, |Im|) (non-negative floats compare as ints)
+__global__ void bank_maxabs_kernel(const float2 *__restrict__ bank, int64_t n, int *out) {
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = bank[i];
+        m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_int(m));
+}
+
+cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    bank_maxabs_kernel<<<152 * 4, 256, 0, st>>>(bank, n, reinterpret_cast<int *>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, const int32_t *tlist, int32_t t0, int32_t nt, int b,
                         int pad, int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st) {
     if (n_gl != kGL) return cudaErrorInvalidValue;
