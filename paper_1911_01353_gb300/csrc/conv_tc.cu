@@ -226,18 +226,28 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     }
     __syncthreads();
     // this thread's spectrum values in the tensor-core mapping: X[seg][r + 64 (16 gcol + i)]
-    float2 xr[16];
+    // Operand-build mapping: thread (ka, blk) forms Z for k = ka + 64 k2, k2 in
+    // [8 blk, 8 blk + 8), of BOTH segments, so each template value is read from
+    // shared memory once per CTA.  It keeps X[s][ka + 64 (8 blk + i)], s = 0, 1.
+    const int ka = tid & 63, blk = tid >> 6;
+    float2 xa[SEGS][8];
     {
-        const float2 *ws = reinterpret_cast<const float2 *>(sm) + seg * WPAD;
-        float m = 0.f;
+        float m[SEGS] = {0.f, 0.f};
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            xr[i] = ws[r + 64 * (16 * gcol + i)];
-            m = fmaxf(m, fmaxf(fabsf(xr[i].x), fabsf(xr[i].y)));
+        for (int s2 = 0; s2 < SEGS; ++s2) {
+            const float2 *ws = reinterpret_cast<const float2 *>(sm) + s2 * WPAD;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                xa[s2][i] = ws[ka + 64 * (8 * blk + i)];
+                m[s2] = fmaxf(m[s2], fmaxf(fabsf(xa[s2][i].x), fabsf(xa[s2][i].y)));
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) atomicMax(&xmax_bits[seg], __float_as_int(m));   // non-negative: int order = float order
+        for (int s2 = 0; s2 < SEGS; ++s2) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m[s2] = fmaxf(m[s2], __shfl_xor_sync(0xffffffffu, m[s2], o));
+            if (lane == 0) atomicMax(&xmax_bits[s2], __float_as_int(m[s2]));   // non-negative: int order = float order
+        }
     }
     __syncthreads();                                          // the work buffers are free from here
     if (tid == 0)
@@ -246,14 +256,17 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             bulk_load(ring + b * L, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + b) * L, (uint32_t)(L * sizeof(float2)),
                       &full[b]);
         }
-    float psc;                                                // power = |y|^2 * psc
+    float psc;                                                // power = |y|^2 * psc (segment seg)
     {
-        const float xm = __int_as_float(xmax_bits[seg]);
         const float cm = __ldg(a.tc_cmax);
-        const float sc = (xm > 0.f && cm > 0.f) ? 1.0f / (xm * cm) : 1.0f;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) xr[i] = make_float2(xr[i].x * sc, xr[i].y * sc);
-        psc = 1.0f / (sc * sc);
+        for (int s2 = 0; s2 < SEGS; ++s2) {
+            const float xm = __int_as_float(xmax_bits[s2]);
+            const float sc = (xm > 0.f && cm > 0.f) ? 1.0f / (xm * cm) : 1.0f;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) xa[s2][i] = make_float2(xa[s2][i].x * sc, xa[s2][i].y * sc);
+            if (s2 == seg) psc = 1.0f / (sc * sc);
+        }
     }
 
     // cells of this thread: n = 64 (16 gcol + i) + r of segment seg
@@ -272,7 +285,9 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         dacc[1][tid] = 0.0;
     }
     float c1 = 0.f, c2 = 0.f;
-    const uint32_t a1_row = smem_u32(sm + OFF_A1) + (row >> 3) * SBO + (row & 7) * 16;
+    // A1 rows 64 s + ka, K chunk blk (re) and 8 + blk (im)
+    const uint32_t a1_r0 = smem_u32(sm + OFF_A1) + (ka >> 3) * SBO + (ka & 7) * 16 + blk * LBO;
+    const uint32_t a1_r1 = a1_r0 + 8 * SBO;
     const uint32_t a3_col = smem_u32(sm + OFF_A3) + (r >> 3) * LBO + (r & 7) * 16 + (8 * seg + 2 * gcol) * SBO;
     const float2 *twt = reinterpret_cast<const float2 *>(sm + OFF_TW);
 
@@ -286,20 +301,26 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     // of the previous template when `issue3`
     auto phase_a = [&](int b, bool issue3) {
         const float2 *C = ring + b * L;
-        uint32_t pr[8], pi[8];
+        uint32_t pr[8], pi[8];                                // [seg 0: 0..3 | seg 1: 4..7]
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-            const float2 z0 = cmul(xr[i], C[r + 64 * (16 * gcol + i)]);
-            const float2 z1 = cmul(xr[i + 1], C[r + 64 * (16 * gcol + i + 1)]);
-            pr[i >> 1] = pack2<PREC>(z0.x, z1.x);
-            pi[i >> 1] = pack2<PREC>(z0.y, z1.y);
-            if (issue3) mma_step<PREC, true>(tmem + 128, sA3, sB, i >> 1);
+        for (int i = 0; i < 8; i += 2) {
+            const float2 c0 = C[ka + 64 * (8 * blk + i)], c1 = C[ka + 64 * (8 * blk + i + 1)];
+#pragma unroll
+            for (int s2 = 0; s2 < SEGS; ++s2) {
+                const float2 z0 = cmul(xa[s2][i], c0), z1 = cmul(xa[s2][i + 1], c1);
+                pr[4 * s2 + (i >> 1)] = pack2<PREC>(z0.x, z1.x);
+                pi[4 * s2 + (i >> 1)] = pack2<PREC>(z0.y, z1.y);
+            }
+            if (issue3) {
+                mma_step<PREC, true>(tmem + 128, sA3, sB, i);
+                mma_step<PREC, true>(tmem + 128, sA3, sB, i + 1);
+            }
         }
         if (issue3) mma_commit(&mbar3);
-        sts128(a1_row + (2 * gcol) * LBO, pr, 0);
-        sts128(a1_row + (2 * gcol + 1) * LBO, pr, 4);
-        sts128(a1_row + (8 + 2 * gcol) * LBO, pi, 0);
-        sts128(a1_row + (9 + 2 * gcol) * LBO, pi, 4);
+        sts128(a1_r0, pr, 0);
+        sts128(a1_r0 + 8 * LBO, pi, 0);
+        sts128(a1_r1, pr, 4);
+        sts128(a1_r1 + 8 * LBO, pi, 4);
     };
     // C: D1 -> twiddle -> A3 (MN-major)
     auto phase_c = [&]() {
