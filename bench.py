@@ -86,7 +86,7 @@ def conv_flops_per_cell(L, V):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("conv.cu", "fft.cuh"):
+    for f in ("conv.cu", "fft.cuh", "device_sync.cuh"):
         with open(os.path.join(ROOT, "paper_1911_01353_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
