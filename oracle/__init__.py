@@ -23,6 +23,11 @@ What it computes, in the order of the paper's pipeline (Adamek et al.,
 7. ``peaks``          thresholded peak finding on the max-projection over
                       (z, w) (Sec. 3 "peak-finding ... above some user
                       specified threshold"; the 1-D peak rule is a reading).
+8. ``power_at``       the filter response at any point (r, z, w) of the
+                      continuous parameter space (the plane off its grid),
+                      by direct summation with rho; ``refine`` takes its
+                      maximum over a small grid around a candidate, and
+                      ``is_peak3d`` compares a cell with its 26 neighbours.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 against closed forms, library routines, invariants or brute force.
@@ -361,6 +366,56 @@ class Result:
     theta: dict = field(default_factory=dict)        # H -> float32
     stats: dict = field(default_factory=dict)        # H -> (mu, sd)
     sums: dict = field(default_factory=dict)         # H -> (fund, S_H fp64)
+
+
+def halfwidth_at(z: float, w: float, pad: int) -> int:
+    """m(z, w) = ceil(|z|/2 + |w|/8) + P for real z, w (equal to
+    ``halfwidth`` on the integer grid)."""
+    return int(math.ceil(abs(z) / 2.0 + abs(w) / 8.0)) + int(pad)
+
+
+def power_at(Fn: np.ndarray, r: float, z: float, w: float, pad: int = 16) -> float:
+    """P(r, z, w) = |sum_k Fn_k conj(rho(k - r; z, w))|^2 over the bins
+    |k - r| <= m(z, w), bins outside [0, N) being zero: the matched-filter
+    power of Sec. 2 at any point of the continuous (r, z, w) space.  On the
+    grid (r = p / b, integer z, w) it is the plane value P(p, z, w), since
+    the taps are c_d = conj(rho(d/b)) with d = b k - p."""
+    Fn = np.asarray(Fn)
+    m = halfwidth_at(z, w, pad)
+    k0 = max(0, int(math.ceil(r - m)))
+    k1 = min(Fn.size - 1, int(math.floor(r + m)))
+    if k1 < k0:
+        return 0.0
+    k = np.arange(k0, k1 + 1, dtype=np.float64)
+    A = np.sum(Fn[k0:k1 + 1].astype(np.complex128) * np.conj(rho(k - r, z, w)))
+    return float(A.real * A.real + A.imag * A.imag)
+
+
+def refine(Fn: np.ndarray, r: float, z: float, w: float, step, half, pad: int = 16):
+    """The largest power_at over the grid (r + i dr, z + j dz, w + l dw),
+    |i| <= hr, |j| <= hz, |l| <= hw: returns (r, z, w, power) of the
+    maximum (first in (i, j, l) order on ties) and the power at the centre."""
+    dr, dz, dw = step
+    hr, hz, hw = half
+    best, centre = None, None
+    for i in range(-hr, hr + 1):
+        for j in range(-hz, hz + 1):
+            for l in range(-hw, hw + 1):
+                pt = (r + i * dr, z + j * dz, w + l * dw)
+                P = power_at(Fn, pt[0], pt[1], pt[2], pad)
+                if i == 0 and j == 0 and l == 0:
+                    centre = P
+                if best is None or P > best[3]:
+                    best = (pt[0], pt[1], pt[2], P)
+    return best, centre
+
+
+def is_peak3d(Fn: np.ndarray, r: float, z: float, w: float, b: int, dz: float, dw: float, pad: int = 16) -> bool:
+    """The cell (r, z, w) is not below any of its 26 neighbours
+    (r +- 1/b, z +- dz, w +- dw): the 3-D local-maximum definition of a
+    peak (a reading; the paper does not define its peak finder)."""
+    (rr, zz, ww, P), c = refine(Fn, r, z, w, (1.0 / b, dz, dw), (1, 1, 1), pad)
+    return c >= P
 
 
 def search(F: np.ndarray, p: Params, bank: Bank | None = None, keep_plane: bool = False):

@@ -292,3 +292,53 @@ def test_sigma_threshold_by_hand():
     S = np.array([[0.0, 2.0, 0.0, 2.0]])          # mu 1, sigma 1
     assert oracle.threshold(p, 0, S) == np.float32(4.0)
     assert oracle.stats(np.array([[1.0, 1.0, 4.0, 6.0]])) == (3.0, math.sqrt(4.5))
+
+
+# ---------------------------------------------------------------------------
+# power at off-grid points (continuous response), refinement, 3-D peaks
+# ---------------------------------------------------------------------------
+
+def test_power_at_zero_z_w_is_truncated_sinc_interpolation():
+    """z = w = 0: rho(q) = sinc(q), so the response at any r is the classic
+    Fourier interpolation sum_k F_k sinc(k - r) over |k - r| <= pad."""
+    rng = np.random.default_rng(11)
+    F = (rng.standard_normal(300) + 1j * rng.standard_normal(300)) / np.sqrt(2)
+    for r in (150.0, 150.5, 150.3, 3.7, 296.2):
+        k = np.arange(300)
+        sel = np.abs(k - r) <= 16
+        A = np.sum(F[sel] * np.sinc(k[sel] - r))
+        assert oracle.power_at(F, r, 0.0, 0.0, pad=16) == pytest.approx(abs(A) ** 2, rel=1e-10, abs=1e-12)
+
+
+def test_power_at_recovers_an_off_grid_chirp():
+    """A noiseless signal F_k = A rho(k - r0; z0, w0): by Cauchy-Schwarz the
+    response peaks at (r0, z0, w0), where it equals A^2 E^2 with E the energy
+    sum_k |rho(k - r0)|^2 of the bins kept (|k - r0| <= m).  Over all k that
+    energy is exactly 1 (Poisson summation + Parseval: rho is the transform
+    of a unit-modulus function on [-1/2, 1/2]), so E -> 1 as the window grows."""
+    r0, z0, w0, A = 200.37, 7.3, 18.6, 3.0
+    k = np.arange(400, dtype=np.float64)
+    F = A * oracle.rho(k - r0, z0, w0)
+    P0 = oracle.power_at(F, r0, z0, w0)
+    m = oracle.halfwidth_at(z0, w0, 16)
+    kk = k[np.abs(k - r0) <= m]
+    E = np.sum(np.abs(oracle.rho(kk - r0, z0, w0)) ** 2)
+    assert P0 == pytest.approx(A * A * E * E, rel=1e-9)
+    assert 0.99 < E < 1.0
+    Ewide = np.sum(np.abs(oracle.rho(k - r0, z0, w0)) ** 2)        # |k - r0| up to ~200 bins
+    assert Ewide == pytest.approx(1.0, abs=2e-3) and Ewide > E
+    for dr, dz, dw in ((0.1, 0, 0), (-0.1, 0, 0), (0, 0.5, 0), (0, -0.5, 0), (0, 0, 3.0), (0, 0, -3.0),
+                       (0.05, 0.2, -1.0)):
+        assert oracle.power_at(F, r0 + dr, z0 + dz, w0 + dw) < P0
+    (r, z, w, P), c = oracle.refine(F, 200.25, 7.0, 20.0, (0.06, 0.15, 0.7), (3, 3, 3))
+    assert abs(r - r0) <= 0.03 and abs(z - z0) <= 0.075 and abs(w - w0) <= 0.35
+    assert P >= c
+
+
+def test_is_peak3d_rules():
+    r0, z0, w0 = 100.0, 4.0, 20.0
+    k = np.arange(220, dtype=np.float64)
+    F = oracle.rho(k - r0, z0, w0)
+    assert oracle.is_peak3d(F, r0, z0, w0, 2, 2.0, 20.0)              # the signal's own cell
+    assert not oracle.is_peak3d(F, r0 + 0.5, z0, w0, 2, 2.0, 20.0)    # a neighbour is higher
+    assert not oracle.is_peak3d(F, r0, z0 + 2.0, w0, 2, 2.0, 20.0)
