@@ -90,6 +90,16 @@ typedef struct {
     int32_t item;            /* spectrum of the batch (0 for jerk_search) */
 } jerk_candidate;
 
+/* A candidate refined off the grid (jerk_refine). */
+typedef struct {
+    double  r;               /* Fourier frequency of the largest power evaluated */
+    float   z, w;            /* its z, w */
+    float   power;           /* that power (matched filter of the fundamental, h = 1) */
+    float   power_in;        /* the power at the candidate's own (r, z, w) */
+    int32_t is_peak;         /* 1 if power_in is not below any power evaluated */
+    int32_t reserved;
+} jerk_refined;
+
 /* Read-only description of a plan (sizes derived from the parameters). */
 typedef struct {
     int32_t nz, nw, n_templates;
@@ -183,6 +193,32 @@ jerk_status jerk_search_batch_grid(jerk_plan plan, const void *const *d_specs, c
  * plans are independent for thread-safety purposes, but jerk_templates must
  * not run while another plan on the bank searches. */
 jerk_status jerk_plan_share(jerk_plan parent, const jerk_params *params, jerk_plan *out);
+
+/* Matched-filter power at arbitrary points of the continuous (r, z, w)
+ * space (the response of Sec. 2 off the search grid):
+ *   P(r, z, w) = |sum_k F~_k conj(rho(k - r; z, w))|^2 over |k - r| <= m(z, w),
+ * with F~ the spectrum d_spec (complex64[n], device) normalised as in
+ * jerk_search, bins outside [0, n) zero, m(z, w) = ceil(|z|/2 + |w|/8) +
+ * pad_bins, and rho evaluated by the quadrature of the template bank.  On the
+ * grid (r = p/b, integer z, w) it is the plane value P(p, z, w).  h_rzw is a
+ * host array of `count` triples (r, z, w) (|z| <= 8192, |w| <= 65536); the
+ * powers are written to the host array h_power (FP32, FP64 sums).  Enqueued
+ * on `stream` after the plan's previous work, then synchronised.  Uses the
+ * plan's normalised-spectrum buffer. */
+jerk_status jerk_power_at(jerk_plan plan, const void *d_spec, int64_t n, const double *h_rzw, int64_t count,
+                          float *h_power, void *stream);
+
+/* Refine candidates off the grid: for candidate c, jerk_power_at over the
+ * points (r_c + i h_step[0], z_c + j h_step[1], w_c + l h_step[2]),
+ * |i| <= h_half[0], |j| <= h_half[1], |l| <= h_half[2] (each half <= 64,
+ * steps >= 0), and h_out[c] receives the largest (first in (i, j, l) order on
+ * ties), the power at the candidate's own point and whether that is the
+ * largest.  With steps (1/b, dz, dw) and halves (1, 1, 1) this tests the
+ * candidate against its 26 grid neighbours: a local maximum of the 3-D
+ * power over (r, z, w).  The powers are those of the fundamental (h = 1),
+ * also for candidates of stages H > 1.  count * (grid points) <= 2^26. */
+jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jerk_candidate *h_cands, int32_t count,
+                        const double *h_step, const int32_t *h_half, jerk_refined *h_out, void *stream);
 
 /* Wait for the last search to finish and copy its candidates to h_out
  * (capacity cap records), sorted by (stage position, p).  *n_out receives

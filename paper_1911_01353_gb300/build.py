@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libjerk.so")
-SOURCES = ["plan.cu", "templates.cu", "conv.cu", "conv_tc.cu", "kernels.cu", "noalloc.cu"]
+SOURCES = ["plan.cu", "templates.cu", "conv.cu", "conv_tc.cu", "kernels.cu", "noalloc.cu", "refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(ROOT, "include")]

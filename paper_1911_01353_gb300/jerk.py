@@ -23,7 +23,7 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
-           "jerk_search_batch_grid", "jerk_plan_share")
+           "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -44,6 +44,12 @@ class Candidate(ctypes.Structure):
                 ("z_idx", ctypes.c_int32), ("w_idx", ctypes.c_int32), ("stage", ctypes.c_int32),
                 ("z", ctypes.c_float), ("w", ctypes.c_float), ("power", ctypes.c_float),
                 ("item", ctypes.c_int32)]
+
+
+class Refined(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_double), ("z", ctypes.c_float), ("w", ctypes.c_float),
+                ("power", ctypes.c_float), ("power_in", ctypes.c_float), ("is_peak", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -92,6 +98,10 @@ def lib() -> ctypes.CDLL:
             "jerk_search_batch_grid": ([vp, ctypes.POINTER(vp), ctypes.POINTER(i64), ctypes.POINTER(i32),
                                         ctypes.POINTER(i32), i32, i32, vp], st),
             "jerk_plan_share": ([vp, ctypes.POINTER(Params), ctypes.POINTER(vp)], st),
+            "jerk_power_at": ([vp, vp, i64, ctypes.POINTER(ctypes.c_double), i64, ctypes.POINTER(ctypes.c_float), vp],
+                              st),
+            "jerk_refine": ([vp, vp, i64, ctypes.POINTER(Candidate), i32, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(i32), ctypes.POINTER(Refined), vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -260,6 +270,29 @@ class Plan:
         if code == JERK_EOVERFLOW:
             raise JerkError(code, "jerk_candidates (%d found)" % n.value)
         return [buf[i] for i in range(n.value)]
+
+    def power_at(self, spec, points, stream=None) -> np.ndarray:
+        """Matched-filter power at (r, z, w) points (array of shape (n, 3)) of
+        the complex64 CUDA tensor `spec` (jerk_power_at)."""
+        pts = np.ascontiguousarray(np.asarray(points, dtype=np.float64).reshape(-1, 3))
+        out = np.empty(pts.shape[0], dtype=np.float32)
+        _check(lib().jerk_power_at(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(),
+                                   pts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pts.shape[0],
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _stream_handle(stream)),
+               "jerk_power_at")
+        return out
+
+    def refine(self, spec, cands, step, half, stream=None):
+        """Refined candidates (jerk_refine): `cands` are Candidate records of
+        this spectrum, step = (dr, dz, dw), half = (hr, hz, hw)."""
+        n = len(cands)
+        arr = (Candidate * max(n, 1))(*cands)
+        out = (Refined * max(n, 1))()
+        st = (ctypes.c_double * 3)(*[float(x) for x in step])
+        hf = (ctypes.c_int32 * 3)(*[int(x) for x in half])
+        _check(lib().jerk_refine(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(), arr, n, st, hf, out,
+                                 _stream_handle(stream)), "jerk_refine")
+        return [out[i] for i in range(n)]
 
     def stats(self, item: int = 0):
         k = int(self.params.n_stages)
