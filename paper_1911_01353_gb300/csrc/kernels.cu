@@ -69,7 +69,7 @@ cudaError_t launch_normalise(const float2 *in, float2 *out, int64_t n, int B, cu
 // the max keeps the lowest t on ties.  HBM-bound: each slot float is read once.
 // ---------------------------------------------------------------------------
 template <int NS>
-__global__ void __launch_bounds__(256) harmonic_kernel(HarmArgs a, bool stats) {
+__global__ void __launch_bounds__(256, 4) harmonic_kernel(HarmArgs a, bool stats) {
     __shared__ double red[JERK_MAX_STAGES][2][8];
     const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
     int top = 0;   // highest stage index defined at p0
