@@ -389,7 +389,8 @@ def serve_bench(a):
 
     t0 = time.perf_counter()
     srv = serve.Server(300, 900, dz=dz, dw=dw, stages=(1,), thresh=(19.0,), thresh_mode=jerk.THRESH_SIGMA,
-                       n_workers=a.workers, worker_bins=1 << 24, max_batch=32, max_candidates=1 << 22)
+                       n_workers=a.workers, worker_bins=1 << 24, max_batch=32, max_candidates=1 << 22,
+                       precision=a.precision)
     bank_s = time.perf_counter() - t0
     bus = getattr(torch.cuda.get_device_properties(0), "pci_bus_id", None)
     clk = ClockSampler(str(bus) if bus is not None else None)
@@ -406,7 +407,8 @@ def serve_bench(a):
     sv, pl = out["served"][0], out["plain"][0]
     line = {"metric": METRIC + "; p50/p99 latency", "value": sv["cells_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": sv["seconds"] * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": ("f32", "bf16", "f16")[a.precision],
+            "data": "synthetic",
             "config": {"workload": "serving: Poisson %.0f req/s for %.0f s, n = 2^U(18,23) bins, zmax in "
                                    "{50,100,200,300}, wmax in {0,300,600,900}, one (300, 900) bank of %d "
                                    "templates, stage 1" % (a.rate, a.duration, srv.bank.info.n_templates),

@@ -220,6 +220,15 @@ jerk_status jerk_power_at(jerk_plan plan, const void *d_spec, int64_t n, const d
 jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jerk_candidate *h_cands, int32_t count,
                         const double *h_step, const int32_t *h_half, jerk_refined *h_out, void *stream);
 
+/* Exercise the failure path of the device waits: after the plan's previous
+ * work, one GPU thread waits, with the bounded wait the filter kernels use on
+ * their bulk copies and tensor-core products, on a barrier phase that nothing
+ * completes.  After limit_us microseconds (1 .. 10^6) it gives up and sets the
+ * plan's device error flag, as a filter CTA does.  Synchronises and returns
+ * what jerk_candidates would: JERK_ETIMEOUT (the flag is then cleared, and the
+ * plan and its context stay usable).  No other device state changes. */
+jerk_status jerk_check_waits(jerk_plan plan, int32_t limit_us, void *stream);
+
 /* Wait for the last search to finish and copy its candidates to h_out
  * (capacity cap records), sorted by (stage position, p).  *n_out receives
  * the number found.  If it exceeds cap (JERK_EOVERFLOW, first cap records

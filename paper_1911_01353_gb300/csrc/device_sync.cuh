@@ -42,13 +42,18 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-// wait for phase `parity` of `bar`, giving up after ~1 s
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// wait for phase `parity` of `bar`, giving up after limit_ns of %globaltimer
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
+}
+
+// the filter kernels' wait: give up after ~1 s
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    return mbar_wait_for(bar, parity, 1000000000ull);
 }
 
 // OR of `pred` over the `n` threads of named barrier `id` (also a barrier)

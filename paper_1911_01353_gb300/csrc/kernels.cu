@@ -1,6 +1,7 @@
 // Normalisation, harmonic sum, statistics and peak finding.
 #include <cfloat>
 
+#include "device_sync.cuh"
 #include "jerk_internal.h"
 
 namespace jerk {
@@ -309,6 +310,23 @@ cudaError_t launch_peaks(const PeakArgs &a, cudaStream_t st) {
     if (nblk < 1) nblk = 1;
     dim3 grid((unsigned)nblk, (unsigned)a.n_stages);
     peaks_kernel<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Failure-path check: one thread waits, with the filter kernels' bounded
+// wait, on a phase of an mbarrier that nothing completes; when the limit
+// expires it sets the device error flag exactly as a filter CTA would, and
+// returns.  Nothing else runs in the kernel.
+// ---------------------------------------------------------------------------
+__global__ void wait_check_kernel(int *err, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    mbar_init(&bar, 1);
+    if (!mbar_wait_for(&bar, 0, limit_ns)) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_check(int *err, uint64_t limit_ns, cudaStream_t st) {
+    wait_check_kernel<<<1, 1, 0, st>>>(err, limit_ns);
     return cudaGetLastError();
 }
 

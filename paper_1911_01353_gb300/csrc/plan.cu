@@ -1275,6 +1275,17 @@ jerk_status jerk_phase_times(jerk_plan pl, float *h_ms, int32_t n) {
     return JERK_OK;
 }
 
+jerk_status jerk_check_waits(jerk_plan pl, int32_t limit_us, void *stream) {
+    if (!pl || limit_us < 1 || limit_us > 1000000) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    JCHECK(launch_wait_check(pl->d_err, (uint64_t)limit_us * 1000ull, st));
+    JCHECK(cudaEventRecord(pl->done, st));
+    JCHECK(cudaEventSynchronize(pl->done));
+    return device_error(pl);          // JERK_ETIMEOUT, and the flag is cleared for the next search
+}
+
 jerk_status jerk_stats(jerk_plan pl, int32_t item, double *h_mean, double *h_std, float *h_theta) {
     if (!pl) return JERK_EINVAL;
     if (!pl->searched) return JERK_ESTATE;

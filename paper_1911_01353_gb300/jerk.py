@@ -23,7 +23,7 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
-           "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine")
+           "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
                               st),
             "jerk_refine": ([vp, vp, i64, ctypes.POINTER(Candidate), i32, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(i32), ctypes.POINTER(Refined), vp], st),
+            "jerk_check_waits": ([vp, i32, vp], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -293,6 +294,14 @@ class Plan:
         _check(lib().jerk_refine(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(), arr, n, st, hf, out,
                                  _stream_handle(stream)), "jerk_refine")
         return [out[i] for i in range(n)]
+
+    def check_waits(self, limit_us: int = 20000, stream=None) -> int:
+        """Status code of jerk_check_waits (JERK_ETIMEOUT when the bounded
+        device wait and its error report work); argument errors raise."""
+        code = int(lib().jerk_check_waits(self._h, int(limit_us), _stream_handle(stream)))
+        if code == JERK_EINVAL:
+            _check(code, "jerk_check_waits")
+        return code
 
     def stats(self, item: int = 0):
         k = int(self.params.n_stages)

@@ -134,7 +134,7 @@ class Server:
 
     def __init__(self, zmax, wmax, dz=2, dw=20, stages=(1,), thresh=(8.0,), thresh_mode=jerk.THRESH_SIGMA,
                  n_workers=4, worker_bins=1 << 24, max_batch=32, max_candidates=1 << 20, device=0,
-                 reserve_bytes=4 << 30, small_cells=2e10, max_large=2, seg_len=0):
+                 reserve_bytes=4 << 30, small_cells=2e10, max_large=2, seg_len=0, precision=0):
         import torch
         self.torch = torch
         self.device = device
@@ -144,7 +144,7 @@ class Server:
         torch.cuda.set_device(device)
         p = jerk.make_params(zmax, dz, wmax, dw, stages=stages, thresh=thresh, thresh_mode=thresh_mode,
                              seg_len=seg_len, max_bins=worker_bins, max_candidates=max_candidates,
-                             max_batch=max_batch)
+                             max_batch=max_batch, precision=precision)
         self.params = p
         self.bank = jerk.Plan(p, device=device)                      # builds the bank
         torch.cuda.synchronize(device)
