@@ -172,10 +172,10 @@ class ClockSampler:
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(wl, spec, budget_s=12.0, stride=16, cells=65536):
+def oracle_sample(wl, spec, seconds=12.0, stride=16, cells=65536):
     """Time the FP64 oracle's direct correlation (plus the spectrum's
     normalisation) on templates t = 0, stride, 2 stride, ... over `cells`
-    consecutive cells in the middle of the spectrum, until budget_s elapses.
+    consecutive cells in the middle of the spectrum, until seconds elapses.
     Returns (cells/s, cells done, threads, description)."""
     import oracle
     op = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages)
@@ -192,7 +192,7 @@ def oracle_sample(wl, spec, budget_s=12.0, stride=16, cells=65536):
         _ = o.real * o.real + o.imag * o.imag
         done += cells
         used.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > budget_s:
+        if time.perf_counter() - t_start > seconds:
             break
     corr_s = sum(used)
     desc = ("FP64 direct correlation of the normalised spectrum with %d templates "
@@ -249,7 +249,7 @@ def reference_arm(a):
     times, cells = [], 0
     for i in range(a.warmup + a.steps):
         t0 = time.perf_counter()
-        v, n, th, desc = oracle_sample(wl, spec, budget_s=6.0, stride=97)
+        v, n, th, desc = oracle_sample(wl, spec, seconds=6.0, stride=97)
         dt = time.perf_counter() - t0
         if i >= a.warmup:
             times.append(n / v)

@@ -69,7 +69,7 @@ def test_next_batch_small_first_then_large_fifo():
     assert not small and [r.rid for r in b] == [0]           # plain form: the oldest, whatever its size
 
 
-def test_pick_batch_cell_budget():
+def test_pick_batch_cell_limit():
     cost = lambda r: r.n                                     # noqa: E731
     w = [req(0, 60), req(1, 30), req(2, 20)]
     assert [r.rid for r in serve.pick_batch(w, 1000, 8, 90, cost)] == [0, 1]
