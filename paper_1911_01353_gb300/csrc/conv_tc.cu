@@ -387,14 +387,24 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 const int q0 = seg0 + 64 * 16 * gcol + r;
                 int quo = q0 / h, rem = q0 - quo * h;
                 const int dq = 64 / h, dr = 64 - dq * h;
+                if (dr == 0) {
+                    // h divides 64 (h = 1, 2, 4, 8): the thread's cells are all
+                    // harmonics of this h, or none is
+                    if (rem == 0) {
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    if (((vmask >> i) & 1u) && rem == 0 && quo < len) dst[quo] = P[i] * psc;
-                    quo += dq;
-                    rem += dr;
-                    if (rem >= h) {
-                        rem -= h;
-                        quo += 1;
+                        for (int i = 0; i < 16; ++i)
+                            if (((vmask >> i) & 1u) && quo + i * dq < len) dst[quo + i * dq] = P[i] * psc;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        if (((vmask >> i) & 1u) && rem == 0 && quo < len) dst[quo] = P[i] * psc;
+                        quo += dq;
+                        rem += dr;
+                        if (rem >= h) {
+                            rem -= h;
+                            quo += 1;
+                        }
                     }
                 }
             }
