@@ -43,8 +43,8 @@ SM_MAX_MHZ = 2070.0
 def args_():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=("paper", "small", "dm", "serve"), default="paper",
                     help="paper: one 2^22-bin spectrum; small: 2^16 bins; dm: 64 uneven DM-trial spectra "
@@ -489,6 +489,10 @@ def main():
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
+    # FP32 FMA rate and L2 read bandwidth of this GPU (microbenchmarks, outside the timed region)
+    f32, l2 = pkg.measure_peaks(local)
+    measured_peaks = {"fp32_fma_tflops": f32, "l2_read_gbs": l2,
+                      "note": "microbenchmarks: independent FMA chains on every SM; 64 MB read 20x from L2"}
 
     props = torch.cuda.get_device_properties(local)
     bus = None
@@ -535,7 +539,8 @@ def main():
             "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
             "frac": achieved / peak_alu, "traffic": traffic,
             "flops_per_cell": conv_flops_per_cell(L, V),
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+            "measured": measured_peaks}
     accuracy = None
     if a.precision:
         # tensor pipe: two 64-point DFT blocks per point and transform, 8 flops per

@@ -220,6 +220,13 @@ jerk_status jerk_power_at(jerk_plan plan, const void *d_spec, int64_t n, const d
 jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jerk_candidate *h_cands, int32_t count,
                         const double *h_step, const int32_t *h_half, jerk_refined *h_out, void *stream);
 
+/* Measure, on `device`, two roofline denominators the filter kernels are
+ * judged against: the FP32 FMA rate (every SM busy with independent FMA
+ * chains; *fp32_tflops counts 2 flops per FMA) and the L2 read bandwidth (a
+ * 64 MB buffer read 20 times with 16-byte loads, *l2_gbs).  Takes about
+ * 100 ms; allocates and frees 64 MB. */
+jerk_status jerk_measure_peaks(int device, double *fp32_tflops, double *l2_gbs);
+
 /* Exercise the failure path of the device waits: after the plan's previous
  * work, one GPU thread waits, with the bounded wait the filter kernels use on
  * their bulk copies and tensor-core products, on a barrier phase that nothing

@@ -3,5 +3,5 @@
 The search runs in the hand-written CUDA kernels of ``libjerk.so`` behind
 the C ABI in ``include/jerk.h``; ``jerk`` is its ctypes binding.
 """
-from .jerk import (THRESH_ABS, THRESH_SIGMA, Candidate, Info, JerkError, Params, Plan, lib,  # noqa: F401
-                   make_params)
+from .jerk import (THRESH_ABS, THRESH_SIGMA, Candidate, Info, JerkError, Params, Plan, Refined,  # noqa: F401
+                   lib, make_params, measure_peaks)

@@ -110,6 +110,7 @@ cudaError_t launch_finalise_stats(const double *part1, int64_t n1, const double 
                                   double *stats_out, float *theta_out, cudaStream_t st);
 cudaError_t launch_peaks(const PeakArgs &a, cudaStream_t st);
 cudaError_t launch_wait_check(int *err, uint64_t limit_ns, cudaStream_t st);
+cudaError_t measure_peaks(int sms, double *fp32_tflops, double *l2_gbs);
 
 // host helpers
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);

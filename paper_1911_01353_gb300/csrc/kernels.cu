@@ -330,4 +330,83 @@ cudaError_t launch_wait_check(int *err, uint64_t limit_ns, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Microbenchmarks for the roofline denominators that are not measured
+// elsewhere: FP32 FMA throughput (8 independent FMA chains per thread, every
+// SM full) and L2 read bandwidth (a buffer smaller than L2 read repeatedly
+// with 16-byte loads).  Their outputs are consumed so nothing is elided.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) fma_peak_kernel(float *out, int iters, float a, float b) {
+    float x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (float)(threadIdx.x + i) * 1e-3f;
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = fmaf(x[i], a, b);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == 12345.678f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // practically never
+}
+
+__global__ void __launch_bounds__(256) l2_read_kernel(const float4 *__restrict__ buf, int64_t n4, int reps,
+                                                      float *out) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+            const float4 v = __ldcg(buf + i);                 // cached in L2 only
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
+        }
+    if (acc.x + acc.y + acc.z + acc.w == 12345.678f) out[threadIdx.x] = acc.x;
+}
+
+cudaError_t measure_peaks(int sms, double *fp32_tflops, double *l2_gbs) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float *scratch = nullptr;
+    float4 *buf = nullptr;
+    const int64_t n4 = (64ll << 20) / 16;                    // 64 MB: inside the 129 MB L2
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(float) * 512 * sms * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&buf, sizeof(float4) * n4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0, sizeof(float4) * n4, st);
+    float ms = 0.f;
+    const int blocks = sms * 4, iters = 4096;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
+        cudaEventRecord(e0, st);
+        fma_peak_kernel<<<blocks, 512, 0, st>>>(scratch, iters, 0.999f, 1e-4f);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e == cudaSuccess)
+        *fp32_tflops = 2.0 * 8 * 16 * (double)iters * blocks * 512 / (ms * 1e-3) / 1e12;
+    const int reps = 20;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, st);
+        l2_read_kernel<<<sms * 8, 256, 0, st>>>(buf, n4, reps, scratch);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (e == cudaSuccess) *l2_gbs = (double)n4 * 16 * reps / (ms * 1e-3) / 1e9;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaFree(buf);
+    cudaFree(scratch);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return e;
+}
+
 }  // namespace jerk

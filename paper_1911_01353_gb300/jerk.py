@@ -23,7 +23,8 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_candidates", "jerk_plan_destroy", "jerk_status_str", "jerk_plan_info",
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
-           "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits")
+           "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits",
+           "jerk_measure_peaks")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
             "jerk_refine": ([vp, vp, i64, ctypes.POINTER(Candidate), i32, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(i32), ctypes.POINTER(Refined), vp], st),
             "jerk_check_waits": ([vp, i32, vp], st),
+            "jerk_measure_peaks": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                                   st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -110,6 +113,13 @@ def lib() -> ctypes.CDLL:
             fn.restype = res
         _lib = L
     return _lib
+
+
+def measure_peaks(device: int = 0):
+    """(FP32 TFLOP/s, L2 read GB/s) measured on `device` (jerk_measure_peaks)."""
+    f, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().jerk_measure_peaks(device, ctypes.byref(f), ctypes.byref(b)), "jerk_measure_peaks")
+    return f.value, b.value
 
 
 class JerkError(RuntimeError):
