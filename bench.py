@@ -247,9 +247,10 @@ def reference_arm(a):
     wl = workload(a.workload, a.bins)
     spec = wl.make()
     times, cells = [], 0
+    per_step = max(0.5, min(6.0, 120.0 / max(1, a.warmup + a.steps)))   # the whole run: about 2 minutes
     for i in range(a.warmup + a.steps):
         t0 = time.perf_counter()
-        v, n, th, desc = oracle_sample(wl, spec, seconds=6.0, stride=97)
+        v, n, th, desc = oracle_sample(wl, spec, seconds=per_step, stride=97)
         dt = time.perf_counter() - t0
         if i >= a.warmup:
             times.append(n / v)
