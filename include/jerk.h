@@ -182,7 +182,8 @@ jerk_status jerk_search_batch(jerk_plan plan, const void *const *d_specs, const 
 jerk_status jerk_search_batch_grid(jerk_plan plan, const void *const *d_specs, const int64_t *n, const int32_t *zmax,
                                    const int32_t *wmax, int32_t count, int32_t flags, void *stream);
 
-/* A new plan that uses `parent`'s template bank (not copied; jerk_templates
+/* (No counterpart in the paper, which searches one spectrum at a time.)
+ * A new plan that uses `parent`'s template bank (not copied; jerk_templates
  * on either plan fills it for both) with its own workspace, candidate buffer
  * and thresholds, so several searches over one bank can be in flight at once
  * (one per plan, each on its own stream).  params must equal the parent's in
@@ -208,7 +209,9 @@ jerk_status jerk_plan_share(jerk_plan parent, const jerk_params *params, jerk_pl
 jerk_status jerk_power_at(jerk_plan plan, const void *d_spec, int64_t n, const double *h_rzw, int64_t count,
                           float *h_power, void *stream);
 
-/* Refine candidates off the grid: for candidate c, jerk_power_at over the
+/* Refine candidates off the grid (Sec. 2's response evaluated between the
+ * grid points; the paper keeps candidates on its grid and defines no
+ * refinement or 3-D peak rule): for candidate c, jerk_power_at over the
  * points (r_c + i h_step[0], z_c + j h_step[1], w_c + l h_step[2]),
  * |i| <= h_half[0], |j| <= h_half[1], |l| <= h_half[2] (each half <= 64,
  * steps >= 0), and h_out[c] receives the largest (first in (i, j, l) order on
@@ -220,14 +223,16 @@ jerk_status jerk_power_at(jerk_plan plan, const void *d_spec, int64_t n, const d
 jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jerk_candidate *h_cands, int32_t count,
                         const double *h_step, const int32_t *h_half, jerk_refined *h_out, void *stream);
 
-/* Measure, on `device`, two roofline denominators the filter kernels are
+/* (No counterpart in the paper.)  Measure, on `device`, two roofline
+ * denominators the filter kernels are
  * judged against: the FP32 FMA rate (every SM busy with independent FMA
  * chains; *fp32_tflops counts 2 flops per FMA) and the L2 read bandwidth (a
  * 64 MB buffer read 20 times with 16-byte loads, *l2_gbs).  Takes about
  * 100 ms; allocates and frees 64 MB. */
 jerk_status jerk_measure_peaks(int device, double *fp32_tflops, double *l2_gbs);
 
-/* Exercise the failure path of the device waits: after the plan's previous
+/* (No counterpart in the paper.)  Exercise the failure path of the device
+ * waits: after the plan's previous
  * work, one GPU thread waits, with the bounded wait the filter kernels use on
  * their bulk copies and tensor-core products, on a barrier phase that nothing
  * completes.  After limit_us microseconds (1 .. 10^6) it gives up and sets the
