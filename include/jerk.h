@@ -224,21 +224,20 @@ jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jer
                         const double *h_step, const int32_t *h_half, jerk_refined *h_out, void *stream);
 
 /* (No counterpart in the paper.)  Measure, on `device`, two roofline
- * denominators the filter kernels are
- * judged against: the FP32 FMA rate (every SM busy with independent FMA
- * chains; *fp32_tflops counts 2 flops per FMA) and the L2 read bandwidth (a
- * 64 MB buffer read 20 times with 16-byte loads, *l2_gbs).  Takes about
- * 100 ms; allocates and frees 64 MB. */
+ * denominators the filter kernels are judged against: the FP32 FMA rate
+ * (every SM busy with independent FMA chains; *fp32_tflops counts 2 flops per
+ * FMA) and the L2 read bandwidth (a 64 MB buffer read 20 times with 16-byte
+ * loads, *l2_gbs).  Takes about 100 ms; allocates and frees 64 MB. */
 jerk_status jerk_measure_peaks(int device, double *fp32_tflops, double *l2_gbs);
 
 /* (No counterpart in the paper.)  Exercise the failure path of the device
- * waits: after the plan's previous
- * work, one GPU thread waits, with the bounded wait the filter kernels use on
- * their bulk copies and tensor-core products, on a barrier phase that nothing
- * completes.  After limit_us microseconds (1 .. 10^6) it gives up and sets the
- * plan's device error flag, as a filter CTA does.  Synchronises and returns
- * what jerk_candidates would: JERK_ETIMEOUT (the flag is then cleared, and the
- * plan and its context stay usable).  No other device state changes. */
+ * waits: after the plan's previous work, one GPU thread waits, with the
+ * bounded wait the filter kernels use on their bulk copies and tensor-core
+ * products, on a barrier phase that nothing completes.  After limit_us
+ * microseconds (1 .. 10^6) it gives up and sets the plan's device error flag,
+ * as a filter CTA does.  Synchronises and returns what jerk_candidates would:
+ * JERK_ETIMEOUT (the flag is then cleared, and the plan and its context stay
+ * usable).  No other device state changes. */
 jerk_status jerk_check_waits(jerk_plan plan, int32_t limit_us, void *stream);
 
 /* Wait for the last search to finish and copy its candidates to h_out
