@@ -84,18 +84,21 @@ def conv_flops_per_cell(L, V):
     return (5.0 * L * math.log2(L) + 6.0 * L + 3.0 * V) / V
 
 
-def kernel_hash():
+def kernel_hash(main="conv.cu"):
     h = hashlib.sha256()
-    for f in ("conv.cu", "fft.cuh", "device_sync.cuh"):
+    for f in (main, "fft.cuh", "device_sync.cuh"):
         with open(os.path.join(ROOT, "paper_1911_01353_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(L):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", "conv_paper_scale_traffic.txt")
+def recorded_traffic(L, precision=0):
+    """DRAM bytes per launch of the fused kernel (FP32, or the tensor-core
+    kernel for precision 1/2) from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    name = "conv_paper_scale_traffic.txt" if precision == 0 else "conv_tc_paper_scale_traffic.txt"
+    main = "conv.cu" if precision == 0 else "conv_tc.cu"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -104,7 +107,7 @@ def recorded_traffic(L):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
-    if vals.get("kernel_sha") != kernel_hash() or int(vals.get("seg_len", 0)) != L:
+    if vals.get("kernel_sha") != kernel_hash(main) or int(vals.get("seg_len", 0)) != L:
         return None
     try:
         return float(vals["dram_bytes_per_full_launch"])
@@ -533,7 +536,7 @@ def main():
     flops = conv_flops_per_cell(L, V) * cells
     peak_alu = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12    # TFLOP/s, FP32 FMA
     achieved = flops / (conv_ms / 1e3) / 1e12
-    traffic = recorded_traffic(L)
+    traffic = recorded_traffic(L, a.precision)
     peaks, peaks_src = peaks_file()
 
     roof = {"bound": "alu", "kernel": "conv_kernel (fused FFT-multiply-IFFT-power)",
@@ -552,7 +555,7 @@ def main():
         roof = {"bound": "tensor", "kernel": "conv_tc_kernel (DFT blocks on tcgen05, %s operands)"
                                              % ("BF16" if a.precision == 1 else "FP16"),
                 "achieved": t_achieved, "peak": t_peak, "unit": "TFLOP/s", "frac": t_achieved / t_peak,
-                "traffic": None, "flops_per_cell": tflops_cell,
+                "traffic": traffic, "flops_per_cell": tflops_cell,
                 "peak_source": "%s dense bf16 (sustained), FP16 at the same rate" % peaks_src,
                 "alu_view": {"achieved": achieved, "peak": peak_alu, "frac": achieved / peak_alu,
                              "note": "FP32-equivalent transform flops (5 L log2 L + 6 L + 3 V per segment)"}}
