@@ -1,0 +1,181 @@
+"""Parity at the benchmark's full size, in the configuration bench.py times:
+a 2^22-bin spectrum with 8 injected chirps, zmax 200 / wmax 600 (12 261
+templates, L = 4096), stages 1-2-4-8, SIGMA thresholds T = 19, 17, 15, 14.
+
+The oracle cannot compute the 411 GB plane, so it checks sampled outputs one
+by one (direct correlation in FP64) and properties that hold at any size:
+
+* plane rows of boundary and random templates (jerk_plane, the search's own
+  kernel in plane-write mode) at thousands of sampled cells;
+* the max-projections of every stage at sampled cells: the value equals the
+  oracle's power (or harmonic sum) of the reported argmax, and bounds the
+  oracle's value at many other templates (fundamentals);
+* every stage-1 candidate's power equals the oracle's at its (p, t), and the
+  candidates satisfy the peak rule on the GPU's own max-projection;
+* the injected signals show in the max-projection at their frequencies;
+* the statistics are those of unit noise (mean = tap energy, sigma = mean)
+  and grow as H and sqrt(H) over the stages.
+
+Tolerance: PLANE_TOL of the plane maximum per power, H times that for a sum
+of H powers; the reduced-precision filters with their own bounds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import PLANE_TOL, jerk_params, lib_ready
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+T_SIGMA = (19.0, 17.0, 15.0, 14.0)
+TC_TOL = {1: 1e-2, 2: 1e-3}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return lib_ready()
+
+
+@pytest.fixture(scope="module")
+def full(pkg):
+    wl = synth.paper_scale()
+    F = wl.make()
+    op = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages, thresh_mode="sigma", thresh=T_SIGMA)
+    Fn = oracle.normalise(F, op.norm_block)
+    x = torch.from_numpy(F).cuda()
+    plan = pkg.Plan(jerk_params(op, F.size, max_candidates=1 << 20))
+    plan.search(x)
+    cands = plan.candidates()
+    M = [plan.maxproj(si) for si in range(len(op.stages))]          # (value, argmax t) per stage
+    stats = plan.stats(0)
+    yield dict(wl=wl, F=F, Fn=Fn, op=op, x=x, plan=plan, cands=cands, M=M, stats=stats)
+    plan.close()
+
+
+def test_full_size_plane_rows(full):
+    op, Fn, plan, x = full["op"], full["Fn"], full["plan"], full["x"]
+    T, bN = op.n_templates, 2 * full["F"].size
+    rng = np.random.default_rng(21)
+    picks = [0, T - 1, op.nz - 1, T - op.nz, T // 2] + [int(t) for t in rng.choice(T, 3, replace=False)]
+    bank = oracle.Bank(op, templates=picks)
+    scale = float(full["M"][0][0].max())                              # the plane maximum
+    tol = PLANE_TOL * scale
+    sig = [int(2 * s.r) for s in full["wl"].signals]
+    out = torch.empty(bN, dtype=torch.float32, device="cuda")
+    for t in picks:
+        plan.plane(x, t, 1, out)
+        row = out.cpu().numpy()
+        ps = np.concatenate([rng.integers(0, bN, 3000), [0, 1, bN - 2, bN - 1],
+                             np.concatenate([np.arange(p - 8, p + 9) for p in sig])])
+        want = bank.power_cells(Fn, np.full(ps.size, t), ps)
+        err = np.abs(row[ps].astype(np.float64) - want)
+        assert err.max() <= tol, (t, float(err.max()), tol)
+
+
+def test_full_size_maxproj_samples(full):
+    op, Fn, M = full["op"], full["Fn"], full["M"]
+    rng = np.random.default_rng(22)
+    bN = 2 * full["F"].size
+    tol = PLANE_TOL * float(M[0][0].max())
+    cand_p = [int(c.p) for c in full["cands"] if c.stage == 1][:40]
+    cells = np.concatenate([rng.integers(0, bN, 60), cand_p]).astype(np.int64)
+    # stage 1: the argmax's power equals M1; random templates never exceed it
+    R = [int(t) for t in rng.choice(op.n_templates, 600, replace=False)]
+    arg = [int(M[0][1][p]) for p in cells]
+    bank = oracle.Bank(op, templates=sorted(set(R) | set(arg)))
+    got = M[0][0][cells].astype(np.float64)
+    at_arg = bank.power_cells(Fn, arg, cells)
+    assert np.max(np.abs(at_arg - got)) <= tol
+    tt = np.repeat(np.array(R), cells.size)
+    pp = np.tile(cells, len(R))
+    others = bank.power_cells(Fn, tt, pp).reshape(len(R), cells.size)
+    assert np.all(others <= got[None, :] + tol)
+    # stages H > 1: S_H(p, f) = sum_h P(h p, t(h z_f, h w_f))
+    for si, H in enumerate(op.stages):
+        if H == 1:
+            continue
+        fund, harm = oracle.stage_templates(op, H)
+        ncell = (bN - 1) // H + 1
+        cs = np.concatenate([rng.integers(0, ncell, 40), rng.integers(max(0, ncell - 50), ncell, 4)])
+        row_of = {int(f): i for i, f in enumerate(fund)}
+        fr = [int(f) for f in rng.choice(fund, min(150, fund.size), replace=False)]
+        argf = [int(M[si][1][p]) for p in cs]
+        need = sorted({int(t) for f in set(fr) | set(argf) for t in harm[row_of[f]]})
+        bk = oracle.Bank(op, templates=need)
+
+        def S(fs, ps):
+            tot = np.zeros(len(fs))
+            for h in range(1, H + 1):
+                tot += bk.power_cells(Fn, [harm[row_of[f]][h - 1] for f in fs], [h * p for p in ps])
+            return tot
+
+        gotH = M[si][0][cs].astype(np.float64)
+        assert np.max(np.abs(S(argf, cs) - gotH)) <= H * tol, H
+        fs = np.repeat(np.array(fr), cs.size)
+        ps = np.tile(cs, len(fr))
+        assert np.all(S(list(fs), list(ps)).reshape(len(fr), cs.size) <= gotH[None, :] + H * tol), H
+
+
+def test_full_size_candidates(full):
+    op, Fn, M, cands = full["op"], full["Fn"], full["M"], full["cands"]
+    tol = PLANE_TOL * float(M[0][0].max())
+    mu, sd, theta = full["stats"]
+    c1 = [c for c in cands if c.stage == 1]
+    assert c1
+    bank = oracle.Bank(op, templates=sorted({int(c.t) for c in c1}))
+    want = bank.power_cells(Fn, [int(c.t) for c in c1], [int(c.p) for c in c1])
+    assert np.max(np.abs(want - np.array([c.power for c in c1]))) <= tol
+    for si, H in enumerate(op.stages):
+        Mv = M[si][0]
+        for c in (c for c in cands if c.stage == H):
+            p = int(c.p)
+            assert Mv[p] > theta[si] and Mv[p] == np.float32(c.power)
+            assert p == 0 or Mv[p] > Mv[p - 1]
+            assert p + 1 == Mv.size or Mv[p] >= Mv[p + 1]
+    # the injected signals stand out in the stage-1 max-projection at their frequencies,
+    # and those clearly above the threshold are candidates
+    for s in full["wl"].signals:
+        lo, hi = int(2 * s.r) - 4, int(2 * s.r) + 5
+        peak = float(M[0][0][lo:hi].max())
+        assert peak >= 0.5 * s.snr, (s.r, s.snr, peak)
+        if peak > theta[0] + 2 * tol:
+            assert any(lo <= c.p < hi for c in c1), (s.r, peak)
+
+
+def test_full_size_statistics(full):
+    mu, sd, theta = full["stats"]
+    op = full["op"]
+    assert 0.98 < mu[0] < 1.01 and 0.97 < sd[0] / mu[0] < 1.05           # Exp-like unit noise
+    for si, H in enumerate(op.stages):
+        assert mu[si] == pytest.approx(H * mu[0], rel=0.03)
+        assert sd[si] == pytest.approx(math.sqrt(H) * sd[0], rel=0.05)
+        assert theta[si] == pytest.approx(mu[si] + T_SIGMA[si] * sd[si], rel=1e-5)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_size_tensor_core_rows(full, pkg, prec):
+    op, Fn, x = full["op"], full["Fn"], full["x"]
+    T, bN = op.n_templates, 2 * full["F"].size
+    # plane rows do not depend on the stages: a stage-1 plan needs no harmonic-row workspace
+    op1 = oracle.Params(op.zmax, op.dz, op.wmax, op.dw, stages=(1,), thresh=(20.0,))
+    p = jerk_params(op1, full["F"].size)
+    p.precision = prec
+    rng = np.random.default_rng(23)
+    picks = [0, T // 2, int(rng.integers(T))]
+    bank = oracle.Bank(op, templates=picks)
+    scale = float(full["M"][0][0].max())
+    out = torch.empty(bN, dtype=torch.float32, device="cuda")
+    with pkg.Plan(p) as plan:
+        for t in picks:
+            plan.plane(x, t, 1, out)
+            ps = rng.integers(0, bN, 3000)
+            want = bank.power_cells(Fn, np.full(ps.size, t), ps)
+            err = np.abs(out.cpu().numpy()[ps].astype(np.float64) - want)
+            assert err.max() <= TC_TOL[prec] * scale, (prec, t, float(err.max()) / scale)
