@@ -179,3 +179,65 @@ def test_full_size_tensor_core_rows(full, pkg, prec):
             want = bank.power_cells(Fn, np.full(ps.size, t), ps)
             err = np.abs(out.cpu().numpy()[ps].astype(np.float64) - want)
             assert err.max() <= TC_TOL[prec] * scale, (prec, t, float(err.max()) / scale)
+
+
+def test_dm_batch_configuration(pkg):
+    """The batched configuration (zmax 200, wmax 300: 6 231 templates, stages
+    1-2-4-8, SIGMA), three DM-trial spectra of 2^20 - 2^21 bins in one graph-
+    replayed launch: each item's candidates are exactly its own search's, and
+    the oracle agrees with sampled max-projection cells and every stage-1
+    candidate's power."""
+    trials = synth.dm_trials(3, seed=3, lo=20.0, hi=21.0)
+    specs = [synth.spectrum(n, seed, sigs) for n, seed, sigs in trials]
+    op = oracle.Params(200, 2, 300, 20, stages=(1, 2, 4, 8), thresh_mode="sigma", thresh=T_SIGMA)
+    p = jerk_params(op, sum(s.size for s in specs), max_candidates=1 << 20)
+    p.max_batch = len(specs)
+    rng = np.random.default_rng(24)
+    with pkg.Plan(p) as plan:
+        dev = [torch.from_numpy(s).cuda() for s in specs]
+        alone = []
+        for x in dev:
+            plan.search(x)
+            alone.append([(c.stage, c.p, c.t, c.power) for c in plan.candidates()])
+        plan.search_batch(dev, graph=True)
+        plan.search_batch(dev, graph=True)                             # the replay
+        recs = plan.candidates()
+        Ms = [plan.maxproj(0, item=i) for i in range(len(specs))]
+    for i, F in enumerate(specs):
+        mine = [(c.stage, c.p, c.t, c.power) for c in recs if c.item == i]
+        assert mine == alone[i], i
+        Fn = oracle.normalise(F, op.norm_block)
+        M, t = Ms[i]
+        tol = PLANE_TOL * float(M.max())
+        cells = rng.integers(0, M.size, 80)
+        c1 = [c for c in recs if c.item == i and c.stage == 1]
+        bank = oracle.Bank(op, templates=sorted({int(t[p]) for p in cells} | {int(c.t) for c in c1}))
+        assert np.max(np.abs(bank.power_cells(Fn, t[cells], cells) - M[cells])) <= tol
+        if c1:
+            want = bank.power_cells(Fn, [int(c.t) for c in c1], [int(c.p) for c in c1])
+            assert np.max(np.abs(want - np.array([c.power for c in c1]))) <= tol
+
+
+def test_served_size_subgrid_request(pkg):
+    """A serving-size request: the (300, 900) bank (27 391 templates) searches
+    a 2^22-bin spectrum over its (200, 600) sub-grid at stage 1, as the server
+    does; sampled cells and every candidate agree with the oracle's direct
+    correlation, and every reported template lies inside the sub-grid."""
+    wl = synth.paper_scale()
+    F = wl.make()
+    op = oracle.Params(300, 2, 900, 20, stages=(1,), thresh_mode="sigma", thresh=(19.0,))
+    with pkg.Plan(jerk_params(op, F.size, max_candidates=1 << 20)) as plan:
+        plan.search_batch([torch.from_numpy(F).cuda()], zmax=[200], wmax=[600], transient=True)
+        recs = plan.candidates()
+        M, t = plan.maxproj(0)
+    Fn = oracle.normalise(F, op.norm_block)
+    tol = PLANE_TOL * float(M.max())
+    rng = np.random.default_rng(25)
+    cells = rng.integers(0, M.size, 80)
+    zt, wt = oracle.grid(op)
+    assert all(abs(zt[t[p]]) <= 200 and abs(wt[t[p]]) <= 600 for p in cells)
+    assert recs and all(abs(c.z) <= 200 and abs(c.w) <= 600 for c in recs)
+    bank = oracle.Bank(op, templates=sorted({int(t[p]) for p in cells} | {int(c.t) for c in recs}))
+    assert np.max(np.abs(bank.power_cells(Fn, t[cells], cells) - M[cells])) <= tol
+    want = bank.power_cells(Fn, [int(c.t) for c in recs], [int(c.p) for c in recs])
+    assert np.max(np.abs(want - np.array([c.power for c in recs]))) <= tol
