@@ -208,6 +208,12 @@ conv_kernel(ConvArgs a) {
     const auto twi = make_tw<LOG2L, +1>(twtab, j);
     const int rv = fft_rev<LOG2L>(j);
     unsigned vmask = 0;
+    // Cells r < RSAFE of every thread of this segment are valid (within V and
+    // the spectrum) when V >= NT RSAFE and the segment ends before bN; the
+    // statistics then mask only r >= RSAFE.  The flag is uniform over the
+    // segment, so over each warp.
+    constexpr int RSAFE = 13;
+    bool vfast;
     {
         const int64_t bN = itm->bN;
 #pragma unroll
@@ -215,6 +221,7 @@ conv_kernel(ConvArgs a) {
             const int cell = rv + NT * r;
             if (cell < V && seg0 + cell < bN) vmask |= 1u << r;
         }
+        vfast = V >= NT * RSAFE && (int64_t)seg0 + NT * RSAFE <= bN;
     }
 
     float mx[16];
@@ -236,16 +243,20 @@ conv_kernel(ConvArgs a) {
         const int t = __ldg(a.order + k);                     // template index
         const int b = it % NBUF;
         const float2 *tsm = smem + b * L;
+        // A thread whose wait expired reads a buffer that may still be landing;
+        // its values are discarded: the whole segment leaves at the barrier below.
         const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(it / NBUF) & 1u);
-        if (named_any(1 + half, NT, !ok)) {                   // also orders reuse of `work`
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = cmul(xr[m], tsm[j + NT * m]);
+        fft_pass0<LOG2L, +1>(v, twi);
+        // One barrier per template over the segment's threads: it reports an
+        // expired wait, ends this segment's reads of the buffer, and orders the
+        // previous template's reads of `work` and `stage` before their reuse.
+        if (named_any(1 + half, NT, !ok)) {
             if (j == 0) atomicExch(a.err, 1);
             failed = true;
             break;
         }
-#pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = cmul(xr[m], tsm[j + NT * m]);
-        fft_pass0<LOG2L, +1>(v, twi);
-        bar_half();                                           // this segment is done with the buffer
         if (j == 0) __threadfence_block();
         if (j == 0 && atomicAdd(&rel[b], 1) == SEGS - 1) {
             rel[b] = 0;
@@ -276,8 +287,13 @@ conv_kernel(ConvArgs a) {
             if constexpr (STATS) {
                 // invalid cells (overlap, beyond the spectrum) count as 0; the staged
                 // row is never read back at those cells
+                if (vfast) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                    for (int r = RSAFE; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                }
                 float c1 = facc[0][tid] + tree16(P);
                 float sq[8];
 #pragma unroll

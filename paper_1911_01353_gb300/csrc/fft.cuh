@@ -310,6 +310,15 @@ __device__ __forceinline__ void fft_store0(const float2 (&a)[16], float2 *__rest
 }
 
 // passes 1..NP; leaves y[rev(j) + NT r] in a[r]
+//
+// Pass s reads sub-problems of nprev = N0 / 16^(s-1) points, each handled by
+// nprev / 16 consecutive threads, and (if not last) writes its outputs back
+// into the same region.  So the hazards before a pass's loads (written by the
+// previous pass's groups of 16 nprev / 16 = nprev threads) and before its
+// stores (read by its own nprev / 16 threads) involve one warp only when
+// those groups fit in a warp; there __syncwarp orders them and `bar` (the
+// barrier over all threads of the transform) is not needed.  Pass 1's loads
+// read what fft_store0 wrote across the whole transform: always `bar`.
 template <int LOG2L, int SIGN, class Tw, class Bar>
 __device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ work, int j, const Tw &tw,
                                          Bar bar) {
@@ -319,7 +328,10 @@ __device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ w
     for (int s = 1; s <= C::NP; ++s) {
         const int ns = nprev / 16;
         const int rho = j / ns, fp = j & (ns - 1);
-        bar();
+        if (s > 1 && nprev <= 32)
+            __syncwarp();
+        else
+            bar();
         {
             const float2 *r = work + pad16(rho * nprev + fp);
             const int step = ns + (ns >> 4);
@@ -329,7 +341,10 @@ __device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ w
         dft16<SIGN>(a);
         if (s < C::NP) {
             tw.applys(a, s);
-            bar();
+            if (nprev <= 512)
+                __syncwarp();
+            else
+                bar();
             float2 *w = work + pad16(rho * 16 * ns + fp);
             const int step = ns + (ns >> 4);
 #pragma unroll
