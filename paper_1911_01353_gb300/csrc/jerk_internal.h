@@ -79,6 +79,7 @@ struct HarmArgs {
     unsigned long long *M[JERK_MAX_STAGES];
     double *stat_part;                     // [gridDim.x][n_stages][2]
     int32_t f_chunk;                       // fundamentals per block (y split)
+    int *err;                              // set on an expired wait (JERK_ETIMEOUT)
 };
 
 struct PeakArgs {
@@ -103,8 +104,8 @@ cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int 
 cudaError_t launch_conv_tc(int precision, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
 cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, cudaStream_t st);
 int conv_segs_per_cta(int log2L);
-cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats,
-                            cudaStream_t st);
+cudaError_t launch_harmonic(const HarmArgs &a, int nblk_y, bool stats, cudaStream_t st);
+int harmonic_cells_per_block();
 cudaError_t launch_finalise_stats(const double *part1, int64_t n1, const double *partH, int64_t nH,
                                   int n_stages, const double *counts, const float *thresh, int mode,
                                   double *stats_out, float *theta_out, cudaStream_t st);

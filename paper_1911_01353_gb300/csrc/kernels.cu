@@ -62,151 +62,283 @@ cudaError_t launch_normalise(const float2 *in, float2 *out, int64_t n, int B, cu
 
 // ---------------------------------------------------------------------------
 // Harmonic sum (Sec. 3 names it; S_H(p, z, w) = sum_{h=1..H} P(h p, h z, h w)
-// is the reading) and the stage-H max-projection over (z, w).  Each thread
-// owns 4 consecutive fundamental cells p and loops over the fundamentals in
-// ascending t; the harmonic rows P(h p, h z, h w) were written by the fused
-// kernel into per-(h, fundamental) slots indexed by p (128-byte aligned), so
-// every read is a coalesced 16-byte load.  Sums are FP32 in fixed h order;
-// the max keeps the lowest t on ties.  HBM-bound: each slot float is read once.
+// is the reading) and the stage-H max-projection over (z, w).  The harmonic
+// rows P(h p, h z, h w) were written by the fused kernel into per-(h,
+// fundamental) slots indexed by p (128-byte aligned).  A block covers
+// HC_CELLS consecutive fundamental cells: HC_THREADS consumer threads own
+// HC_PT cells each, and one producer warp streams the block's chunk of every
+// row it needs (fundamentals in ascending t, h ascending) from HBM into a
+// ring of HR shared-memory slots with bulk copies (cp.async.bulk +
+// mbarrier), so HR x 8 KB are in flight per block whatever the consumers
+// do.  The producer stages 32 table entries at a time in shared memory and
+// one lane issues the copies, writing each slot's (t, top stage) beside it.
+// Consumers sum their cells of each row in fixed h order (FP32), keep
+// (max, argmax) per stage (lowest t on ties) and the statistics partials,
+// and release each slot per warp.  Every wait is bounded (about one
+// second); on expiry the block sets the error flag and leaves after its
+// copies in flight have landed.
 // ---------------------------------------------------------------------------
+constexpr int HC_THREADS = 256;                 // consumer threads
+constexpr int HC_PT = 8;                        // cells per consumer thread (two float4)
+constexpr int HC_CELLS = HC_PT * HC_THREADS;    // fundamental cells per block
+constexpr int HR = 11;                          // ring slots, one row chunk (HC_CELLS floats) each:
+                                                // two blocks (ring + statics) fit an SM's shared memory
+
+struct HarmEntry {                              // a table entry as the producer stages it
+    int64_t off[JERK_MAX_HARMONIC];
+    int t, st;
+};
+
 template <int NS>
-__global__ void __launch_bounds__(256, 4) harmonic_kernel(HarmArgs a, bool stats) {
-    __shared__ double red[JERK_MAX_STAGES][2][8];
-    const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    int top = 0;   // highest stage index defined at p0
+__global__ void __launch_bounds__(HC_THREADS + 32, 2) harmonic_kernel(HarmArgs a, bool stats) {
+    extern __shared__ __align__(128) float4 ring[];   // [HR][HC_CELLS / 4]
+    __shared__ __align__(8) uint64_t full[HR];        // row chunk landed
+    __shared__ __align__(8) uint64_t empty[HR];       // every consumer warp done with the slot
+    __shared__ int2 meta[HR];                         // (t, top stage) of the slot's fundamental
+    __shared__ HarmEntry tab[32];                     // the producer's current table entries
+    __shared__ double red[JERK_MAX_STAGES][2][HC_THREADS / 32];
+    __shared__ double dacc[NS - 1][2][HC_THREADS];    // per-thread FP64 statistics of stages 1.. (kept out of registers)
+    constexpr int Q = HC_CELLS / 4;                   // float4 per slot
+    const int tid = threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.x * HC_CELLS;
+    int topb = 0;   // highest stage index with cells in this block
 #pragma unroll
     for (int si = 1; si < NS; ++si)
-        if (p0 < a.n_cells[si]) top = si;
-    bool ok[NS][4];
-#pragma unroll
-    for (int si = 1; si < NS; ++si)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) ok[si][c] = p0 + c < a.n_cells[si];
-    float mx[NS][4];
-    int am[NS][4];
-    double d1[NS], d2[NS];
-    float c1[NS], c2[NS];
-#pragma unroll
-    for (int si = 0; si < NS; ++si) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            mx[si][c] = -1.0f;
-            am[si][c] = 0;
-        }
-        d1[si] = d2[si] = 0.0;
-        c1[si] = c2[si] = 0.f;
-    }
+        if (c0 < a.n_cells[si]) topb = si;
     int hlo[NS], hhi[NS];
 #pragma unroll
     for (int si = 1; si < NS; ++si) {
         hlo[si] = si == 1 ? 1 : a.stages[si - 1] + 1;
         hhi[si] = a.stages[si];
     }
+    if (tid < HR) {
+        mbar_init(&full[tid], 1);
+        mbar_init(&empty[tid], HC_THREADS / 32);
+    }
+    __syncthreads();
     const int f0 = blockIdx.y * a.f_chunk;
     const int f1 = min(a.n_fund, f0 + a.f_chunk);
-    if (top > 0) {
-        int cnt = 0;
-#pragma unroll 2
-        for (int f = f0; f < f1; ++f) {
-            const FundEntry *fe = a.fund + f;
-            const int t = __ldg(&fe->t);
-            const int st = min(__ldg(&fe->top_stage), top);
-            float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    if (tid >= HC_THREADS) {
+        // ---- producer warp ----
+        const int plane = tid - HC_THREADS;
+        uint32_t bytes[NS];   // chunk bytes of a stage-si row: rows hold n_cells[si] cells, padded to 32
 #pragma unroll
-            for (int si = 1; si < NS; ++si) {
-                if (si <= st) {
+        for (int si = 1; si < NS; ++si) {
+            const int64_t avail = ((a.n_cells[si] + 3) & ~(int64_t)3) - c0;
+            bytes[si] = (uint32_t)(4 * (avail < HC_CELLS ? (avail > 0 ? avail : 0) : HC_CELLS));
+        }
+        int slot = 0, round = 0, issued = 0;
+        bool good = topb > 0;
+        for (int fb = f0; fb < f1 && good; fb += 32) {
+            const int f = fb + plane;
+            if (f < f1) {
+                const FundEntry *fe = a.fund + f;
+                const int st = min(__ldg(&fe->top_stage), topb);
+                const int H = a.stages[st];
+                tab[plane].t = __ldg(&fe->t);
+                tab[plane].st = st;
 #pragma unroll
-                    for (int h = 1; h <= JERK_MAX_HARMONIC; ++h) {
-                        if (h >= hlo[si] && h <= hhi[si]) {
-                            const float4 v = __ldg(reinterpret_cast<const float4 *>(
-                                a.slots + __ldg(&fe->off[h - 1]) + p0));
-                            s.x += v.x;
-                            s.y += v.y;
-                            s.z += v.z;
-                            s.w += v.w;
-                        }
-                    }
-                    const float sv[4] = {s.x, s.y, s.z, s.w};
+                for (int h = 0; h < JERK_MAX_HARMONIC; ++h)
+                    if (h < H) tab[plane].off[h] = __ldg(&fe->off[h]);
+            }
+            __syncwarp();
+            if (plane == 0) {
+                const int nb = min(32, f1 - fb);
+                for (int k = 0; k < nb && good; ++k) {
+                    const int t = tab[k].t, st = tab[k].st;
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        if (ok[si][c] && sv[c] > mx[si][c]) {
-                            mx[si][c] = sv[c];
-                            am[si][c] = t;
-                        }
-                        if (stats && ok[si][c]) {
-                            c1[si] += sv[c];
-                            c2[si] = fmaf(sv[c], sv[c], c2[si]);
+                    for (int si = 1; si < NS; ++si) {
+                        if (si <= st) {
+                            for (int h = hlo[si]; h <= hhi[si] && good; ++h) {
+                                if (round > 0 && !mbar_wait_bounded(&empty[slot], (uint32_t)(round - 1) & 1u)) {
+                                    good = false;
+                                    break;
+                                }
+                                meta[slot] = make_int2(t, st);
+                                bulk_load(ring + slot * Q, a.slots + tab[k].off[h - 1] + c0, bytes[si], &full[slot]);
+                                ++issued;
+                                if (++slot == HR) {
+                                    slot = 0;
+                                    ++round;
+                                }
+                            }
                         }
                     }
                 }
             }
-            if (stats && ++cnt == 16) {
-                cnt = 0;
+            good = __shfl_sync(0xffffffffu, good, 0);
+            __syncwarp();   // lane 0 done reading `tab`
+        }
+        if (plane == 0) {
+            if (topb > 0 && !good) atomicExch(a.err, 1);
+            // never leave with a copy still writing into this block's shared memory:
+            // the last phase of each slot in use
+            const int last = issued < HR ? issued : HR;
+            for (int k = 0; k < last; ++k) {
+                const int i = issued - 1 - k;
+                mbar_wait_bounded(&full[i % HR], (uint32_t)(i / HR) & 1u);
+            }
+        }
+    } else {
+        // ---- consumers: thread tid owns cells p0 + 4u + c, u = 0..HC_PT/4-1 ----
+        constexpr int U = HC_PT / 4;
+        const int lane = tid & 31;
+        const int64_t p0 = c0 + 4 * tid;
+        float mx[NS][HC_PT];
+        int am[NS][HC_PT];
+        float c1[NS], c2[NS];
+#pragma unroll
+        for (int si = 0; si < NS; ++si) {
+#pragma unroll
+            for (int c = 0; c < HC_PT; ++c) {
+                mx[si][c] = -1.0f;
+                am[si][c] = 0;
+            }
+            if (si > 0) dacc[si - 1][0][tid] = dacc[si - 1][1][tid] = 0.0;
+            c1[si] = c2[si] = 0.f;
+        }
+        // cell of (u, c): p0 + 4 HC_THREADS u + c
+        auto cell_ok = [&](int si, int k) { return p0 + 4 * HC_THREADS * (k >> 2) + (k & 3) < a.n_cells[si]; };
+        if (topb > 0) {
+            int slot = 0, cnt = 0;
+            uint32_t phase = 0;
+            bool good = true;
+            // every table entry has a top stage >= 1, so every fundamental has rows
+            for (int f = f0; f < f1 && good; ++f) {
+                // the fundamental's first row carries its (t, top stage)
+                if (!mbar_wait_bounded(&full[slot], phase)) {
+                    good = false;
+                    break;
+                }
+                const int2 tm = meta[slot];
+                const int t = tm.x, st = tm.y;
+                float sv[HC_PT];
+#pragma unroll
+                for (int c = 0; c < HC_PT; ++c) sv[c] = 0.f;
 #pragma unroll
                 for (int si = 1; si < NS; ++si) {
-                    d1[si] += (double)c1[si];
-                    d2[si] += (double)c2[si];
-                    c1[si] = c2[si] = 0.f;
+                    if (si <= st && good) {
+                        for (int h = hlo[si]; h <= hhi[si]; ++h) {
+                            if (!mbar_wait_bounded(&full[slot], phase)) {
+                                good = false;
+                                break;
+                            }
+                            float4 v[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) v[u] = ring[slot * Q + u * HC_THREADS + tid];
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&empty[slot]);
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                sv[4 * u] += v[u].x;
+                                sv[4 * u + 1] += v[u].y;
+                                sv[4 * u + 2] += v[u].z;
+                                sv[4 * u + 3] += v[u].w;
+                            }
+                            if (++slot == HR) {
+                                slot = 0;
+                                phase ^= 1u;
+                            }
+                        }
+                        if (!good) break;
+#pragma unroll
+                        for (int c = 0; c < HC_PT; ++c) {
+                            const bool ok = cell_ok(si, c);
+                            if (ok && sv[c] > mx[si][c]) {
+                                mx[si][c] = sv[c];
+                                am[si][c] = t;
+                            }
+                            if (stats && ok) {
+                                c1[si] += sv[c];
+                                c2[si] = fmaf(sv[c], sv[c], c2[si]);
+                            }
+                        }
+                    }
+                }
+                if (stats && ++cnt == 16) {
+                    cnt = 0;
+#pragma unroll
+                    for (int si = 1; si < NS; ++si) {
+                        dacc[si - 1][0][tid] += (double)c1[si];
+                        dacc[si - 1][1][tid] += (double)c2[si];
+                        c1[si] = c2[si] = 0.f;
+                    }
+                }
+            }
+            if (!good) {
+                if (lane == 0) atomicExch(a.err, 1);
+            } else {
+#pragma unroll
+                for (int si = 1; si < NS; ++si) {
+#pragma unroll
+                    for (int c = 0; c < HC_PT; ++c) {
+                        if (cell_ok(si, c) && mx[si][c] >= 0.f) {
+                            const int64_t p = p0 + 4 * HC_THREADS * (c >> 2) + (c & 3);
+                            const unsigned long long packed =
+                                ((unsigned long long)__float_as_uint(mx[si][c]) << 32) |
+                                (unsigned long long)(0xFFFFFFFFu - (unsigned)am[si][c]);
+                            if (gridDim.y == 1)
+                                a.M[si][p] = packed;
+                            else
+                                atomicMax(a.M[si] + p, packed);
+                        }
+                    }
                 }
             }
         }
+        if (stats) {
+            const int warp = tid >> 5;
 #pragma unroll
-        for (int si = 1; si < NS; ++si) {
+            for (int si = 1; si < NS; ++si) {
+                double x1 = dacc[si - 1][0][tid] + (double)c1[si], x2 = dacc[si - 1][1][tid] + (double)c2[si];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (ok[si][c] && mx[si][c] >= 0.f) {
-                    const unsigned long long packed =
-                        ((unsigned long long)__float_as_uint(mx[si][c]) << 32) |
-                        (unsigned long long)(0xFFFFFFFFu - (unsigned)am[si][c]);
-                    if (gridDim.y == 1)
-                        a.M[si][p0 + c] = packed;
-                    else
-                        atomicMax(a.M[si] + p0 + c, packed);
+                for (int o = 16; o > 0; o >>= 1) {
+                    x1 += __shfl_xor_sync(0xffffffffu, x1, o);
+                    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+                }
+                if (lane == 0) {
+                    red[si][0][warp] = x1;
+                    red[si][1][warp] = x2;
                 }
             }
         }
     }
-    if (stats) {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
+    __syncthreads();
+    if (stats && tid == 0) {
+        const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
         for (int si = 1; si < NS; ++si) {
-            double x1 = d1[si] + (double)c1[si], x2 = d2[si] + (double)c2[si];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                x1 += __shfl_xor_sync(0xffffffffu, x1, o);
-                x2 += __shfl_xor_sync(0xffffffffu, x2, o);
+            double s1 = 0.0, s2 = 0.0;
+            for (int w = 0; w < HC_THREADS / 32; ++w) {
+                s1 += red[si][0][w];
+                s2 += red[si][1][w];
             }
-            if (lane == 0) {
-                red[si][0][warp] = x1;
-                red[si][1][warp] = x2;
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-            for (int si = 1; si < NS; ++si) {
-                double s1 = 0.0, s2 = 0.0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                    s1 += red[si][0][w];
-                    s2 += red[si][1][w];
-                }
-                a.stat_part[(blk * a.n_stages + si) * 2] = s1;
-                a.stat_part[(blk * a.n_stages + si) * 2 + 1] = s2;
-            }
+            a.stat_part[(blk * a.n_stages + si) * 2] = s1;
+            a.stat_part[(blk * a.n_stages + si) * 2 + 1] = s2;
         }
     }
 }
 
-cudaError_t launch_harmonic(const HarmArgs &a, int64_t n_threads, int nblk_y, bool stats, cudaStream_t st) {
-    const int64_t nblk = (n_threads + 255) / 256;
-    dim3 grid((unsigned)nblk, (unsigned)nblk_y);
+template <int NS>
+static cudaError_t launch_harmonic_ns(const HarmArgs &a, dim3 grid, bool stats, cudaStream_t st) {
+    const int smem = HR * HC_CELLS * (int)sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(harmonic_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    harmonic_kernel<NS><<<grid, HC_THREADS + 32, smem, st>>>(a, stats);
+    return cudaGetLastError();
+}
+
+int harmonic_cells_per_block() { return HC_CELLS; }
+
+cudaError_t launch_harmonic(const HarmArgs &a, int nblk_y, bool stats, cudaStream_t st) {
+    const int64_t nblk = (a.n_cells[1] + HC_CELLS - 1) / HC_CELLS;
+    const dim3 grid((unsigned)nblk, (unsigned)nblk_y);
     switch (a.n_stages) {
-        case 2: harmonic_kernel<2><<<grid, 256, 0, st>>>(a, stats); break;
-        case 3: harmonic_kernel<3><<<grid, 256, 0, st>>>(a, stats); break;
-        case 4: harmonic_kernel<4><<<grid, 256, 0, st>>>(a, stats); break;
+        case 2: return launch_harmonic_ns<2>(a, grid, stats, st);
+        case 3: return launch_harmonic_ns<3>(a, grid, stats, st);
+        case 4: return launch_harmonic_ns<4>(a, grid, stats, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -218,8 +218,8 @@ int64_t transforms_for(const jerk_plan_s *pl, int64_t n) {
 
 int64_t harm_blocks_for(const jerk_plan_s *pl, int64_t n) {
     if (pl->prm.n_stages < 2) return 0;
-    const int64_t nthreads = (n_cells((int64_t)pl->b * n, pl->prm.stages[1]) + 3) / 4;
-    return (nthreads + 255) / 256;
+    const int64_t cpb = harmonic_cells_per_block();
+    return (n_cells((int64_t)pl->b * n, pl->prm.stages[1]) + cpb - 1) / cpb;
 }
 
 jerk_status validate(const jerk_params *p) {
@@ -626,8 +626,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
             }
             h.stat_part = partH + 2 * ns * L.harm0[i];
             h.f_chunk = L.n_fund[i];
-            const int64_t nthreads = (h.n_cells[1] + 3) / 4;   // 4 cells per thread
-            JCHECK(launch_harmonic(h, nthreads, 1, sigma, st));
+            h.err = pl->d_err;
+            JCHECK(launch_harmonic(h, 1, sigma, st));
         }
     }
     JCHECK(mark(pl, 3, st, capturing));
