@@ -207,6 +207,7 @@ conv_kernel(ConvArgs a) {
     // ---- 2. templates of this group -----------------------------------------
     const auto twi = make_tw<LOG2L, +1>(twtab, j);
     const int rv = fft_rev<LOG2L>(j);
+    const int swz_rv = swzf(rv);
     unsigned vmask = 0;
     // Cells r < RSAFE of every thread of this segment are valid (within V and
     // the spectrum) when V >= NT RSAFE and the segment ends before bN; the
@@ -314,7 +315,13 @@ conv_kernel(ConvArgs a) {
             const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
             if (e0 < e1) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) stage[swzf(rv + NT * r)] = P[r];
+                for (int r = 0; r < 16; ++r) {
+                    // NT r only sets bits >= 8, which swzf neither reads nor changes
+                    if constexpr (NT % 256 == 0)
+                        stage[swz_rv + NT * r] = P[r];
+                    else
+                        stage[swzf(rv + NT * r)] = P[r];
+                }
             }
             if (j == 0) {
                 spend[half][0] = e0;
