@@ -80,15 +80,26 @@ __device__ __forceinline__ int bank_row(const ConvArgs &a, int k) {
     return k;
 }
 
+// A template's harmonic-row slot entries (at most one per h), prefetched into
+// shared memory: harmonic number, row offset (floats) and row length (cells).
+struct RowEntries {
+    int h[JERK_MAX_HARMONIC];
+    int64_t off[JERK_MAX_HARMONIC], len[JERK_MAX_HARMONIC];
+};
+
+// Per-template metadata of the template pipeline, prefetched ahead by cp.async.
+struct TplMeta {
+    int t, e0, e1, pad;
+};
+
 // Store the staged power row of one template into its harmonic-row slots
-// (entries e0..e1): cells q = h p of this segment, p within the row.
-__device__ __forceinline__ void store_rows(const ConvArgs &a, const int64_t *soff, const int64_t *slen,
-                                           const float *pw, const int (*sb)[2], int e0, int e1, int s0, int j,
-                                           int NT) {
-    for (int e = e0; e < e1; ++e) {
-        const int h = __ldg(a.slot_h + e);
-        float *dst = a.slots + __ldg(soff + e);
-        const int len = (int)__ldg(slen + e);
+// (its n entries): cells q = h p of this segment, p within the row.
+__device__ __forceinline__ void store_rows(const ConvArgs &a, const RowEntries &en, int n, const float *pw,
+                                           const int (*sb)[2], int s0, int j, int NT) {
+    for (int e = 0; e < n; ++e) {
+        const int h = en.h[e];
+        float *dst = a.slots + en.off[e];
+        const int len = (int)en.len[e];
         const int pf = sb[h - 1][0];
         const int pl = min(sb[h - 1][1], len - 1);
         if (pl < pf) continue;                                // this segment is past the row's end
@@ -119,7 +130,8 @@ conv_kernel(ConvArgs a) {
     __shared__ double red[2][32];
     __shared__ double dacc[STATS ? 2 : 1][STATS ? ConvCfg<LOG2L>::THREADS : 1];   // FP64 statistics per thread
     __shared__ float facc[STATS ? 2 : 1][STATS ? ConvCfg<LOG2L>::THREADS : 1];    // FP32 partial (32 templates)
-    __shared__ int spend[SEGS][2];                            // slot entries of the staged row
+    __shared__ __align__(16) TplMeta tq[SEGS][4];              // (t, e0, e1) of template k at [k & 3]
+    __shared__ __align__(16) RowEntries rent[SEGS][2];         // slot entries of template k at [k & 1]
 
     const int tid = threadIdx.x;
     const int half = tid / NT;                                // which segment of the CTA
@@ -167,6 +179,12 @@ conv_kernel(ConvArgs a) {
         const int64_t pmax = (bN - 1) / h;
         sbound[half][j][0] = (int)((seg0 + h - 1) / h);
         sbound[half][j][1] = (int)(pl < pmax ? pl : pmax);
+    }
+    if (j == 0 && tb < te) {
+        // the metadata pipeline's first stages (later ones are prefetched in the loop)
+        const int t0 = __ldg(a.order + tb);
+        tq[half][tb & 3] = TplMeta{t0, __ldg(a.slot_beg + t0), __ldg(a.slot_beg + t0 + 1), 0};
+        if (tb + 1 < te) tq[half][(tb + 1) & 3].t = __ldg(a.order + tb + 1);
     }
     __syncthreads();
     if (tid == 0)
@@ -234,14 +252,12 @@ conv_kernel(ConvArgs a) {
         facc[0][tid] = 0.f;
         facc[1][tid] = 0.f;
     }
-    if (j == 0) spend[half][0] = spend[half][1] = 0;
     // Template pipeline: template t sits in buffer b = (t - tb) % NBUF; the
     // last segment of the CTA to finish reading a buffer refills it with
     // template t + NBUF, so the segments never wait on each other.
     bool failed = false;
     for (int k = tb; k < te; ++k) {                         // processing index
         const int it = k - tb;
-        const int t = __ldg(a.order + k);                     // template index
         const int b = it % NBUF;
         const float2 *tsm = smem + b * L;
         // A thread whose wait expired reads a buffer that may still be landing;
@@ -253,6 +269,7 @@ conv_kernel(ConvArgs a) {
         // One barrier per template over the segment's threads: it reports an
         // expired wait, ends this segment's reads of the buffer, and orders the
         // previous template's reads of `work` and `stage` before their reuse.
+        cp_async_wait_all();                                  // the copies issued last template
         if (named_any(1 + half, NT, !ok)) {
             if (j == 0) atomicExch(a.err, 1);
             failed = true;
@@ -268,10 +285,38 @@ conv_kernel(ConvArgs a) {
             }
         }
         fft_store0<LOG2L>(v, work, j);
+        // Metadata pipeline (L2-latency loads kept off the critical path, no
+        // registers held): order[k + 2], then slot_beg of template k + 1, then the
+        // slot entries of template k, each landing before the next template's
+        // first barrier.  Issued here, where the pass-0 values are in shared memory.
+        {
+            const int ne = tq[half][k & 3].e1 - tq[half][k & 3].e0;   // this template's slot entries
+            if (j == 0) {
+                if (k + 2 < te) cp_async<4>(&tq[half][(k + 2) & 3].t, a.order + k + 2);
+                if (k + 1 < te) {
+                    const int t1 = tq[half][(k + 1) & 3].t;
+                    cp_async<4>(&tq[half][(k + 1) & 3].e0, a.slot_beg + t1);
+                    cp_async<4>(&tq[half][(k + 1) & 3].e1, a.slot_beg + t1 + 1);
+                }
+            }
+            if constexpr (MODE == 0) {
+                if (j < ne) {
+                    const int e = tq[half][k & 3].e0 + j;
+                    RowEntries &en = rent[half][k & 1];
+                    cp_async<4>(&en.h[j], a.slot_h + e);
+                    cp_async<8>(&en.off[j], srow[half][0] + e);
+                    cp_async<8>(&en.len[j], srow[half][1] + e);
+                }
+            }
+            cp_async_commit();
+        }
         if constexpr (MODE == 0)
-            if (spend[half][0] < spend[half][1])
-                store_rows(a, srow[half][0], srow[half][1], stage, sbound[half], spend[half][0], spend[half][1],
-                           (int)seg0, j, NT);
+            if (k > tb) {
+                // the previous template's staged row
+                const TplMeta mp = tq[half][(k - 1) & 3];
+                if (mp.e0 < mp.e1)
+                    store_rows(a, rent[half][(k - 1) & 1], mp.e1 - mp.e0, stage, sbound[half], (int)seg0, j, NT);
+            }
         fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
 #pragma unroll
@@ -312,8 +357,7 @@ conv_kernel(ConvArgs a) {
             }
             // harmonic rows of this template: stage the power row now, store it
             // during the next template's transform (whose barriers order it)
-            const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
-            if (e0 < e1) {
+            if (tq[half][k & 3].e0 < tq[half][k & 3].e1) {
 #pragma unroll
                 for (int r = 0; r < 16; ++r) {
                     // NT r only sets bits >= 8, which swzf neither reads nor changes
@@ -323,11 +367,8 @@ conv_kernel(ConvArgs a) {
                         stage[swzf(rv + NT * r)] = P[r];
                 }
             }
-            if (j == 0) {
-                spend[half][0] = e0;
-                spend[half][1] = e1;
-            }
-        } else if (t >= a.t0 && t < a.t0 + a.nt) {
+        } else if (tq[half][k & 3].t >= a.t0 && tq[half][k & 3].t < a.t0 + a.nt) {
+            const int t = tq[half][k & 3].t;
             float *row = a.plane + (int64_t)(t - a.t0) * (2 * (int64_t)a.items[0].N) + seg0;
 #pragma unroll
             for (int r = 0; r < 16; ++r)
@@ -335,11 +376,14 @@ conv_kernel(ConvArgs a) {
         }
     }
 
+    cp_async_wait_all();
     if constexpr (MODE == 0) {
         bar_half();
-        if (!failed && spend[half][0] < spend[half][1])
-            store_rows(a, srow[half][0], srow[half][1], stage, sbound[half], spend[half][0], spend[half][1],
-                       (int)seg0, j, NT);
+        if (!failed && te > tb) {
+            const TplMeta mp = tq[half][(te - 1) & 3];
+            if (mp.e0 < mp.e1)
+                store_rows(a, rent[half][(te - 1) & 1], mp.e1 - mp.e0, stage, sbound[half], (int)seg0, j, NT);
+        }
     }
     __syncthreads();
     if (tid == 0) {
