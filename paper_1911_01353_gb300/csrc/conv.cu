@@ -80,18 +80,6 @@ __device__ __forceinline__ int bank_row(const ConvArgs &a, int k) {
     return k;
 }
 
-// A template's harmonic-row slot entries (at most one per h), prefetched into
-// shared memory: harmonic number, row offset (floats) and row length (cells).
-struct RowEntries {
-    int h[JERK_MAX_HARMONIC];
-    int64_t off[JERK_MAX_HARMONIC], len[JERK_MAX_HARMONIC];
-};
-
-// Per-template metadata of the template pipeline, prefetched ahead by cp.async.
-struct TplMeta {
-    int t, e0, e1, pad;
-};
-
 // Store the staged power row of one template into its harmonic-row slots
 // (its n entries): cells q = h p of this segment, p within the row.
 __device__ __forceinline__ void store_rows(const ConvArgs &a, const RowEntries &en, int n, const float *pw,

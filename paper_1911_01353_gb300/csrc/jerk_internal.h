@@ -69,6 +69,18 @@ struct ConvArgs {
     const float *tc_cmax;    // max over the bank of max(|Re C|, |Im C|)
 };
 
+// A template's harmonic-row slot entries (at most one per h), prefetched into
+// shared memory: harmonic number, row offset (floats) and row length (cells).
+struct RowEntries {
+    int h[JERK_MAX_HARMONIC];
+    int64_t off[JERK_MAX_HARMONIC], len[JERK_MAX_HARMONIC];
+};
+
+// Per-template metadata of the template pipeline, prefetched ahead by cp.async.
+struct TplMeta {
+    int t, e0, e1, pad;
+};
+
 struct HarmArgs {
     const float *slots;
     const FundEntry *fund;
