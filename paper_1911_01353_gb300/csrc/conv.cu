@@ -263,8 +263,10 @@ conv_kernel(ConvArgs a) {
             failed = true;
             break;
         }
-        if (j == 0) __threadfence_block();
-        if (j == 0 && atomicAdd(&rel[b], 1) == SEGS - 1) {
+        // the segment's last warp releases (and, last of the segments, refills) the
+        // buffer: the row stores' uneven last iteration falls on the first warps
+        if (j == NT - 32) __threadfence_block();
+        if (j == NT - 32 && atomicAdd(&rel[b], 1) == SEGS - 1) {
             rel[b] = 0;
             if (k + NBUF < te) {
                 issued[b] += 1;
@@ -278,8 +280,9 @@ conv_kernel(ConvArgs a) {
         // slot entries of template k, each landing before the next template's
         // first barrier.  Issued here, where the pass-0 values are in shared memory.
         {
+            // (spread over warps 1 and 2, away from the buffer release)
             const int ne = tq[half][k & 3].e1 - tq[half][k & 3].e0;   // this template's slot entries
-            if (j == 0) {
+            if (j == 32) {
                 if (k + 2 < te) cp_async<4>(&tq[half][(k + 2) & 3].t, a.order + k + 2);
                 if (k + 1 < te) {
                     const int t1 = tq[half][(k + 1) & 3].t;
@@ -288,12 +291,14 @@ conv_kernel(ConvArgs a) {
                 }
             }
             if constexpr (MODE == 0) {
-                if (j < ne) {
-                    const int e = tq[half][k & 3].e0 + j;
+                constexpr int EW = NT >= 128 ? 64 : 0;        // first thread of the entry copies
+                const int i = j - EW;
+                if (i >= 0 && i < ne) {
+                    const int e = tq[half][k & 3].e0 + i;
                     RowEntries &en = rent[half][k & 1];
-                    cp_async<4>(&en.h[j], a.slot_h + e);
-                    cp_async<8>(&en.off[j], srow[half][0] + e);
-                    cp_async<8>(&en.len[j], srow[half][1] + e);
+                    cp_async<4>(&en.h[i], a.slot_h + e);
+                    cp_async<8>(&en.off[i], srow[half][0] + e);
+                    cp_async<8>(&en.len[i], srow[half][1] + e);
                 }
             }
             cp_async_commit();
