@@ -251,8 +251,14 @@ conv_kernel(ConvArgs a) {
         // A thread whose wait expired reads a buffer that may still be landing;
         // its values are discarded: the whole segment leaves at the barrier below.
         const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(it / NBUF) & 1u);
+        // products in the order pass 0's first radix-4 stage consumes them
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = cmul(xr[m], tsm[j + NT * m]);
+        for (int m1 = 0; m1 < 4; ++m1)
+#pragma unroll
+            for (int m2 = 0; m2 < 4; ++m2) {
+                const int m = m1 + 4 * m2;
+                v[m] = cmul(xr[m], tsm[j + NT * m]);
+            }
         fft_pass0<LOG2L, +1>(v, twi);
         // One barrier per template over the segment's threads: it reports an
         // expired wait, ends this segment's reads of the buffer, and orders the

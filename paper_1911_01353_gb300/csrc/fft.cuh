@@ -333,10 +333,14 @@ __device__ __forceinline__ void fft_rest(float2 (&a)[16], float2 *__restrict__ w
         else
             bar();
         {
+            // loads in the order dft16's first radix-4 stage consumes them
+            // (k1 + 4 k2, k2 fastest), so its butterflies start after four loads
             const float2 *r = work + pad16(rho * nprev + fp);
             const int step = ns + (ns >> 4);
 #pragma unroll
-            for (int k = 0; k < 16; ++k) a[k] = r[k * step];
+            for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+                for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = r[(k1 + 4 * k2) * step];
         }
         dft16<SIGN>(a);
         if (s < C::NP) {
