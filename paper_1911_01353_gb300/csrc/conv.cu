@@ -213,14 +213,12 @@ conv_kernel(ConvArgs a) {
     // ---- 2. templates of this group -----------------------------------------
     const auto twi = make_tw<LOG2L, +1>(twtab, j);
     const int rv = fft_rev<LOG2L>(j);
-    const int swz_rv = swzf(rv);
     unsigned vmask = 0;
-    // Cells r < RSAFE of every thread of this segment are valid (within V and
-    // the spectrum) when V >= NT RSAFE and the segment ends before bN; the
-    // statistics then mask only r >= RSAFE.  The flag is uniform over the
-    // segment, so over each warp.
+    // Bit r of vmask: cell r of this thread is valid (within V and the
+    // spectrum).  Bit 16: cells r < RSAFE of every thread of this segment are
+    // valid (V >= NT RSAFE and the segment ends before bN), so the statistics
+    // mask only r >= RSAFE; it is uniform over the segment, so over each warp.
     constexpr int RSAFE = 13;
-    bool vfast;
     {
         const int64_t bN = itm->bN;
 #pragma unroll
@@ -228,7 +226,7 @@ conv_kernel(ConvArgs a) {
             const int cell = rv + NT * r;
             if (cell < V && seg0 + cell < bN) vmask |= 1u << r;
         }
-        vfast = V >= NT * RSAFE && (int64_t)seg0 + NT * RSAFE <= bN;
+        if (V >= NT * RSAFE && (int64_t)seg0 + NT * RSAFE <= bN) vmask |= 1u << 16;   // bit 16: the fast case
     }
 
     float mx[16];
@@ -332,7 +330,7 @@ conv_kernel(ConvArgs a) {
             if constexpr (STATS) {
                 // invalid cells (overlap, beyond the spectrum) count as 0; the staged
                 // row is never read back at those cells
-                if (vfast) {
+                if (vmask >> 16) {
 #pragma unroll
                     for (int r = RSAFE; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
                 } else {
@@ -361,7 +359,7 @@ conv_kernel(ConvArgs a) {
                 for (int r = 0; r < 16; ++r) {
                     // NT r only sets bits >= 8, which swzf neither reads nor changes
                     if constexpr (NT % 256 == 0)
-                        stage[swz_rv + NT * r] = P[r];
+                        stage[swzf(rv) + NT * r] = P[r];
                     else
                         stage[swzf(rv + NT * r)] = P[r];
                 }
