@@ -271,6 +271,30 @@ def test_other_stage_sets(pkg, stages):
 # edge cases
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("zmax,wmax,stages", [(0, 0, (1, 2, 4, 8)), (0, 20, (1, 2)), (2, 0, (1, 2, 4)),
+                                              (2, 20, (1, 2, 3))])
+def test_degenerate_banks(pkg, zmax, wmax, stages):
+    """Banks of 1 to 9 templates: template groups of one or two (the ends of
+    the per-template metadata pipeline) and, for z = w = 0, one template that
+    is its own h-th harmonic for every h up to 8 (the most harmonic-row
+    entries a template can have).  Every stage and the candidates vs the
+    oracle."""
+    n = 12000
+    F = synth.spectrum(n, 53, [synth.Signal(1000.0, 0.0, 0.0, 25.0, 0.3)], harmonics=8)
+    th = (10.0, 14.0, 18.0, 26.0)[:len(stages)]
+    op = oracle.Params(zmax, 2, wmax, 20, stages=stages, thresh=th)
+    res = oracle.search(F, op, keep_plane=True)
+    tol = PLANE_TOL * res.plane.max()
+    with pkg.Plan(jerk_params(op, n, seg_len=1024)) as plan:
+        assert plan.info.n_templates == op.n_templates
+        cands = _search(pkg, plan, F)
+        for si, H in enumerate(stages):
+            M, t = plan.maxproj(si)
+            compare_maxproj(M, t, *res.maxproj[H], res.sums[H][1], tol)
+    compare_candidates(cands, res, tol)
+    assert any(c.stage == stages[-1] and c.p == 2000 for c in cands)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 1023, 1025])
 def test_tiny_spectra(pkg, n):
     rng = np.random.default_rng(n + 100)
