@@ -16,6 +16,10 @@
 //      max-projection; statistics (SIGMA mode); the harmonic rows the
 //      harmonic sum needs are staged through shared memory and written
 //      coalesced.  In plane mode the power rows are written instead.
+// Each template costs two barriers over its segment's threads; the metadata
+// the epilogue and the row stores need (template index, slot-entry range and
+// entries) is prefetched one template ahead into shared memory by cp.async,
+// and the single-thread duties are spread over the segment's warps.
 //
 // The power plane is never materialised in search mode.  The only wait on
 // another agent is the mbarrier of the bulk copy; it is bounded (about one
