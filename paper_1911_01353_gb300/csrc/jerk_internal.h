@@ -1,6 +1,8 @@
 // Internal declarations shared by the translation units of libjerk.so.
 #pragma once
 
+#include <cstddef>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -80,6 +82,11 @@ struct RowEntries {
 struct TplMeta {
     int t, e0, e1, pad;
 };
+// cp.async copies 4- and 8-byte fields straight into these structs: each field
+// must sit at a multiple of its own size
+static_assert(offsetof(RowEntries, off) % 8 == 0 && offsetof(RowEntries, len) % 8 == 0,
+              "RowEntries: 8-byte fields must be 8-byte aligned");
+static_assert(sizeof(TplMeta) == 16 && offsetof(TplMeta, e0) % 4 == 0, "TplMeta layout");
 
 struct HarmArgs {
     const float *slots;
