@@ -545,6 +545,18 @@ def main():
             "flops_per_cell": conv_flops_per_cell(L, V),
             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
             "measured": measured_peaks}
+    # the second kernel of the step, bound by HBM: every harmonic row is read once
+    # (the plan's row workspace, sized for this spectrum) and M_H written once
+    harm_roof = None
+    harm_ms = statistics.mean(ph["harmonic"] for ph in phases)
+    if harm_ms > 0 and len(wl.stages) > 1:
+        bN = 2 * wl.n_bins
+        h_bytes = 4 * plan.info.slot_floats + 8 * sum((bN - 1) // H + 1 for H in wl.stages[1:])
+        h_gbs = h_bytes / (harm_ms / 1e3) / 1e9
+        harm_roof = {"bound": "hbm", "kernel": "harmonic_kernel (stages > 1)", "achieved": h_gbs,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": h_gbs / peaks["hbm_gbs"],
+                     "bytes_per_launch": h_bytes,
+                     "peak_source": "%s copy bandwidth" % peaks_src}
     accuracy = None
     if a.precision:
         # tensor pipe: two 64-point DFT blocks per point and transform, 8 flops per
@@ -593,6 +605,7 @@ def main():
             "candidates": ncand,
             "templates_s": round(t_templates, 3),
             "roofline": roof,
+            "harmonic_roofline": harm_roof,
             "plain_form_ceiling": {"value": peaks["hbm_gbs"] * 1e9 / 8.0, "unit": UNIT,
                                    "note": "unfused plane write + read, 8 B/cell at %s HBM %.1f GB/s"
                                            % (peaks_src, peaks["hbm_gbs"])},
