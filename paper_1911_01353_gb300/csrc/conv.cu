@@ -288,7 +288,7 @@ conv_kernel(ConvArgs a) {
         // slot entries of template k, each landing before the next template's
         // first barrier.  Issued here, where the pass-0 values are in shared memory.
         {
-            // (spread over warps 1 and 2, away from the buffer release)
+            // (on warps 1 and 2 -- warp 0 at L = 1024 -- away from the buffer release)
             const int ne = tq[half][k & 3].e1 - tq[half][k & 3].e0;   // this template's slot entries
             if (j == 32) {
                 if (k + 2 < te) cp_async<4>(&tq[half][(k + 2) & 3].t, a.order + k + 2);
