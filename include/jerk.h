@@ -240,6 +240,21 @@ jerk_status jerk_measure_peaks(int device, double *fp32_tflops, double *l2_gbs);
  * usable).  No other device state changes. */
 jerk_status jerk_check_waits(jerk_plan plan, int32_t limit_us, void *stream);
 
+/* (No counterpart in the paper.)  Bounds checks of the debug build.  A
+ * library compiled with -DJERK_CHECKS (`python -m paper_1911_01353_gb300.build
+ * --checks`, loaded by the Python binding when JERK_CHECKS=1) checks, before
+ * each global store or copy whose index its kernels compute (harmonic-row
+ * stores, plane rows, max-projection updates, the harmonic sum's row copies),
+ * that the index lies inside the buffer; a failing check skips the access,
+ * counts itself and records its site (the first one).  This call waits for the
+ * plan's work so far and reports the count (*violations), the first site
+ * (*first_site, 0 if none: 1-3 fused filter rows / plane / max-projection,
+ * 4-5 harmonic copy / max-projection, 6-8 tensor-core filter rows / plane /
+ * max-projection) and whether the checks are compiled in (*compiled_in; in the
+ * release build every check is absent and the count stays 0).  Any output may
+ * be NULL.  The counts cover every search of the plan since its creation. */
+jerk_status jerk_check_counts(jerk_plan plan, int64_t *violations, int32_t *first_site, int32_t *compiled_in);
+
 /* Wait for the last search to finish and copy its candidates to h_out
  * (capacity cap records), sorted by (stage position, p).  *n_out receives
  * the number found.  If it exceeds cap (JERK_EOVERFLOW, first cap records

@@ -2,7 +2,13 @@
 
 Every translation unit is compiled in parallel, then linked into
 ``paper_1911_01353_gb300/_build/libjerk.so``.  Usage:
-``python -m paper_1911_01353_gb300.build [--force]``.
+``python -m paper_1911_01353_gb300.build [--force] [--checks]``.
+
+``--checks`` builds the debug library instead,
+``paper_1911_01353_gb300/_build_checks/libjerk.so``, compiled with
+-DJERK_CHECKS: its kernels check the indices of their global stores and
+copies and count violations (``jerk_check_counts``).  The Python binding
+loads it when JERK_CHECKS=1.
 """
 from __future__ import annotations
 
@@ -17,6 +23,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libjerk.so")
+OUT_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(OUT_CHECKS, "libjerk.so")
 SOURCES = ["plan.cu", "templates.cu", "conv.cu", "conv_tc.cu", "kernels.cu", "noalloc.cu", "refine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -34,17 +42,19 @@ def _deps(src: str):
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "jerk.h")]
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    out, lib = (OUT_CHECKS, LIB_CHECKS) if checks else (OUT, LIB)
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
     newest = max(os.path.getmtime(p) for p in _deps(""))
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
-        return LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= newest:
+        return lib
     objs = []
+    extra = ["-DJERK_CHECKS"] if checks else []
 
     def compile_one(src):
-        obj = os.path.join(OUT, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -57,13 +67,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             objs.append(obj)
             if verbose and log:
                 sys.stderr.write(log)
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checks="--checks" in sys.argv))

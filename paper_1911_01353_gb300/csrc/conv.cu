@@ -90,7 +90,8 @@ __device__ __forceinline__ void store_rows(const ConvArgs &a, const RowEntries &
                                            const int (*sb)[2], int s0, int j, int NT) {
     for (int e = 0; e < n; ++e) {
         const int h = en.h[e];
-        float *dst = a.slots + en.off[e];
+        const int64_t off = en.off[e];
+        float *dst = a.slots + off;
         const int len = (int)en.len[e];
         const int pf = sb[h - 1][0];
         const int pl = min(sb[h - 1][1], len - 1);
@@ -100,10 +101,14 @@ __device__ __forceinline__ void store_rows(const ConvArgs &a, const RowEntries &
             // the row is 128-byte aligned), then the ragged end one by one
             const int n4 = (pl - pf + 1) >> 2;
             for (int g = j; g < n4; g += NT)
-                *reinterpret_cast<float4 *>(dst + pf + 4 * g) = *reinterpret_cast<const float4 *>(pw + swzf(4 * g));
-            for (int p = pf + 4 * n4 + j; p <= pl; p += NT) dst[p] = pw[swzf(p - s0)];
+                if (JERK_CHECK(off + pf + 4 * g + 3 < a.slot_cap, a.chk, kChkRowStore))
+                    *reinterpret_cast<float4 *>(dst + pf + 4 * g) =
+                        *reinterpret_cast<const float4 *>(pw + swzf(4 * g));
+            for (int p = pf + 4 * n4 + j; p <= pl; p += NT)
+                if (JERK_CHECK(off + p < a.slot_cap, a.chk, kChkRowStore)) dst[p] = pw[swzf(p - s0)];
         } else {
-            for (int p = pf + j; p <= pl; p += NT) dst[p] = pw[swzf(h * p - s0)];
+            for (int p = pf + j; p <= pl; p += NT)
+                if (JERK_CHECK(off + p < a.slot_cap, a.chk, kChkRowStore)) dst[p] = pw[swzf(h * p - s0)];
         }
     }
 }
@@ -370,10 +375,12 @@ conv_kernel(ConvArgs a) {
             }
         } else if (tq[half][k & 3].t >= a.t0 && tq[half][k & 3].t < a.t0 + a.nt) {
             const int t = tq[half][k & 3].t;
-            float *row = a.plane + (int64_t)(t - a.t0) * (2 * (int64_t)a.items[0].N) + seg0;
+            const int64_t row0 = (int64_t)(t - a.t0) * (2 * (int64_t)a.items[0].N) + seg0;
+            float *row = a.plane + row0;
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                if ((vmask >> r) & 1u) row[rv + NT * r] = P[r];
+                if (((vmask >> r) & 1u) && JERK_CHECK(row0 + rv + NT * r < a.plane_len, a.chk, kChkPlaneStore))
+                    row[rv + NT * r] = P[r];
         }
     }
 
@@ -399,7 +406,8 @@ conv_kernel(ConvArgs a) {
                 const unsigned long long packed =
                     ((unsigned long long)__float_as_uint(mx[r]) << 32) |
                     (unsigned long long)(0xFFFFFFFFu - (unsigned)__ldg(a.order + tb + amx[rv + NT * r]));
-                atomicMax(sM1[half] + seg0 + rv + NT * r, packed);
+                if (JERK_CHECK((int64_t)seg0 + rv + NT * r < itm->bN, a.chk, kChkMaxProj))
+                    atomicMax(sM1[half] + seg0 + rv + NT * r, packed);
             }
         }
         if constexpr (STATS) {

@@ -382,7 +382,8 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
             for (int e = e0; e < e1; ++e) {
                 const int h = __ldg(a.slot_h + e);
-                float *dst = a.slots + __ldg(itm->slot_off + e);
+                const int64_t off = __ldg(itm->slot_off + e);
+                float *dst = a.slots + off;
                 const int len = (int)__ldg(itm->slot_len + e);
                 const int q0 = seg0 + 64 * 16 * gcol + r;
                 int quo = q0 / h, rem = q0 - quo * h;
@@ -393,12 +394,16 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                     if (rem == 0) {
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (((vmask >> i) & 1u) && quo + i * dq < len) dst[quo + i * dq] = P[i] * psc;
+                            if (((vmask >> i) & 1u) && quo + i * dq < len &&
+                                JERK_CHECK(off + quo + i * dq < a.slot_cap, a.chk, kChkTcRowStore))
+                                dst[quo + i * dq] = P[i] * psc;
                     }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        if (((vmask >> i) & 1u) && rem == 0 && quo < len) dst[quo] = P[i] * psc;
+                        if (((vmask >> i) & 1u) && rem == 0 && quo < len &&
+                            JERK_CHECK(off + quo < a.slot_cap, a.chk, kChkTcRowStore))
+                            dst[quo] = P[i] * psc;
                         quo += dq;
                         rem += dr;
                         if (rem >= h) {
@@ -415,10 +420,13 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 mma_commit(&mbar1);
             }
             if (t >= a.t0 && t < a.t0 + a.nt) {
-                float *prow = a.plane + (int64_t)(t - a.t0) * bN + seg0;
+                const int64_t row0 = (int64_t)(t - a.t0) * bN + seg0;
+                float *prow = a.plane + row0;
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    if ((vmask >> i) & 1u) prow[64 * (16 * gcol + i) + r] = P[i] * psc;
+                    if (((vmask >> i) & 1u) &&
+                        JERK_CHECK(row0 + 64 * (16 * gcol + i) + r < a.plane_len, a.chk, kChkTcPlaneStore))
+                        prow[64 * (16 * gcol + i) + r] = P[i] * psc;
             }
         }
     };
@@ -503,7 +511,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                     const int tw = __ldg(a.order + tb + amx_s[seg * L + n]);
                     const unsigned long long packed = ((unsigned long long)__float_as_uint(mx[i] * psc) << 32) |
                                                       (unsigned long long)(0xFFFFFFFFu - (unsigned)tw);
-                    atomicMax(M1 + seg0 + n, packed);
+                    if (JERK_CHECK((int64_t)seg0 + n < bN, a.chk, kChkTcMaxProj)) atomicMax(M1 + seg0 + n, packed);
                 }
             }
         }

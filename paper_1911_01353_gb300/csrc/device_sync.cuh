@@ -72,6 +72,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return mbar_wait_for(bar, parity, 1000000000ull);
 }
 
+// Bounds checks of the debug build (compiled with -DJERK_CHECKS): a failing
+// check adds one to chk[0], records its site in chk[1] if it is the first,
+// and returns false so that the caller skips the access.  In the release
+// build every check is the constant true and costs nothing.
+#ifdef JERK_CHECKS
+__device__ __forceinline__ bool dev_check(bool ok, long long *chk, int site) {
+    if (!ok && chk && atomicAdd(reinterpret_cast<unsigned long long *>(chk), 1ull) == 0ull) chk[1] = site;
+    return ok;
+}
+#define JERK_CHECK(ok, chk, site) ::jerk::dev_check((ok), (chk), (site))
+#else
+#define JERK_CHECK(ok, chk, site) true
+#endif
+
 // OR of `pred` over the `n` threads of named barrier `id` (also a barrier)
 __device__ __forceinline__ bool named_any(int id, int n, bool pred) {
     uint32_t r;

@@ -64,11 +64,26 @@ struct ConvArgs {
     float *slots;
     double *stat_part;       // [gridDim.y][gridDim.x][2]
     int *err;                // set to 1 when a bounded device wait expires
+    int64_t slot_cap;        // floats of `slots` (bounds checks of the debug build)
+    long long *chk;          // violation counter and first site (bounds checks of the debug build)
     // plane mode
     float *plane;            // [nt][bN]
+    int64_t plane_len;       // floats of `plane` (bounds checks of the debug build)
     // reduced-precision (tensor-core) filter
     const void *tc_const;    // 16-bit B operand (32 KB) then the twiddle table (float2 [64][64])
     const float *tc_cmax;    // max over the bank of max(|Re C|, |Im C|)
+};
+
+// Sites of the debug build's bounds checks (the first failing one is recorded).
+enum CheckSite {
+    kChkRowStore = 1,     // fused filter: harmonic-row store
+    kChkPlaneStore = 2,   // fused filter: plane row store (plane mode)
+    kChkMaxProj = 3,      // fused filter: stage-1 max-projection update
+    kChkHarmCopy = 4,     // harmonic sum: bulk copy of a row chunk
+    kChkHarmStore = 5,    // harmonic sum: max-projection store
+    kChkTcRowStore = 6,   // tensor-core filter: harmonic-row store
+    kChkTcPlaneStore = 7, // tensor-core filter: plane row store
+    kChkTcMaxProj = 8,    // tensor-core filter: stage-1 max-projection update
 };
 
 // A template's harmonic-row slot entries (at most one per h), prefetched into
@@ -99,6 +114,8 @@ struct HarmArgs {
     double *stat_part;                     // [gridDim.x][n_stages][2]
     int32_t f_chunk;                       // fundamentals per block (y split)
     int *err;                              // set on an expired wait (JERK_ETIMEOUT)
+    int64_t slot_cap;                      // floats of `slots` (bounds checks of the debug build)
+    long long *chk;                        // violation counter and first site (debug build)
 };
 
 struct PeakArgs {
@@ -229,6 +246,7 @@ struct jerk_plan_s {
     jerk::DevCand *d_cand = nullptr;
     unsigned long long *d_count = nullptr;
     int *d_err = nullptr;              // device error flag (bounded waits)
+    long long *d_chk = nullptr;        // bounds-check violations and first site (debug build)
     double2 *d_gl = nullptr;
     int n_gl = 0;
     int64_t bytes = 0;

@@ -156,7 +156,14 @@ __global__ void __launch_bounds__(HC_THREADS + 32, 2) harmonic_kernel(HarmArgs a
                                     break;
                                 }
                                 meta[slot] = make_int2(t, st);
-                                bulk_load(ring + slot * Q, a.slots + tab[k].off[h - 1] + c0, bytes[si], &full[slot]);
+                                const int64_t src = tab[k].off[h - 1] + c0;
+                                // a skipped copy would leave the consumers waiting: give up
+                                // (bounded) like an expired wait
+                                if (!JERK_CHECK(src >= 0 && src + bytes[si] / 4 <= a.slot_cap, a.chk, kChkHarmCopy)) {
+                                    good = false;
+                                    break;
+                                }
+                                bulk_load(ring + slot * Q, a.slots + src, bytes[si], &full[slot]);
                                 ++issued;
                                 if (++slot == HR) {
                                     slot = 0;
@@ -278,6 +285,7 @@ __global__ void __launch_bounds__(HC_THREADS + 32, 2) harmonic_kernel(HarmArgs a
                             const unsigned long long packed =
                                 ((unsigned long long)__float_as_uint(mx[si][c]) << 32) |
                                 (unsigned long long)(0xFFFFFFFFu - (unsigned)am[si][c]);
+                            if (!JERK_CHECK(p < a.n_cells[si], a.chk, kChkHarmStore)) continue;
                             if (gridDim.y == 1)
                                 a.M[si][p] = packed;
                             else

@@ -296,6 +296,7 @@ void release(jerk_plan_s *pl) {
     cudaFree(pl->d_cand);
     cudaFree(pl->d_count);
     cudaFree(pl->d_err);
+    cudaFree(pl->d_chk);
     cudaFree(pl->d_tc);
     if (pl->h_cand) cudaFreeHost(pl->h_cand);
     if (pl->done) cudaEventDestroy(pl->done);
@@ -602,6 +603,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
     a.slots = pl->d_slots;
     a.stat_part = pl->d_stat_part;
     a.err = pl->d_err;
+    a.chk = pl->d_chk;
+    a.slot_cap = pl->slot_cap;
     a.tc_const = pl->d_tc;
     a.tc_cmax = pl->d_cmax;
     JCHECK(pl->prm.precision ? launch_conv_tc(pl->prm.precision, 0, sigma, a, (int)L.total_ctas, st)
@@ -627,6 +630,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
             h.stat_part = partH + 2 * ns * L.harm0[i];
             h.f_chunk = L.n_fund[i];
             h.err = pl->d_err;
+            h.chk = pl->d_chk;
+            h.slot_cap = pl->slot_cap;
             JCHECK(launch_harmonic(h, 1, sigma, st));
         }
     }
@@ -855,6 +860,8 @@ jerk_status plan_memory(jerk_plan_s *pl, bool own_bank) {
     TRY(dalloc(&pl->bytes, &pl->d_count, 1));
     TRY(dalloc(&pl->bytes, &pl->d_err, 1));
     TRY(cudaMemset(pl->d_err, 0, sizeof(int)));
+    TRY(dalloc(&pl->bytes, &pl->d_chk, 2));
+    TRY(cudaMemset(pl->d_chk, 0, 2 * sizeof(long long)));
     TRY(cudaMallocHost((void **)&pl->h_cand, sizeof(DevCand) * (size_t)params->max_candidates));
     TRY(cudaEventCreateWithFlags(&pl->done, cudaEventDisableTiming));
     TRY(cudaMemcpy(pl->d_thresh, params->thresh, sizeof(float) * JERK_MAX_STAGES, cudaMemcpyHostToDevice));
@@ -1095,6 +1102,8 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
     a.nt = nt;
     a.plane = d_out;
     a.err = pl->d_err;
+    a.chk = pl->d_chk;
+    a.plane_len = (int64_t)nt * 2 * n;
     a.slot_beg = pl->d_slot_beg;
     a.tc_const = pl->d_tc;
     a.tc_cmax = pl->d_cmax;
@@ -1295,6 +1304,22 @@ jerk_status jerk_check_waits(jerk_plan pl, int32_t limit_us, void *stream) {
     JCHECK(cudaEventRecord(pl->done, st));
     JCHECK(cudaEventSynchronize(pl->done));
     return device_error(pl);          // JERK_ETIMEOUT, and the flag is cleared for the next search
+}
+
+jerk_status jerk_check_counts(jerk_plan pl, int64_t *violations, int32_t *first_site, int32_t *compiled_in) {
+    if (!pl) return JERK_EINVAL;
+#ifdef JERK_CHECKS
+    if (compiled_in) *compiled_in = 1;
+#else
+    if (compiled_in) *compiled_in = 0;
+#endif
+    JCHECK(cudaSetDevice(pl->device));
+    JCHECK(cudaEventSynchronize(pl->done));
+    long long c[2] = {0, 0};
+    JCHECK(cudaMemcpy(c, pl->d_chk, sizeof(c), cudaMemcpyDeviceToHost));
+    if (violations) *violations = (int64_t)c[0];
+    if (first_site) *first_site = (int32_t)c[1];
+    return JERK_OK;
 }
 
 jerk_status jerk_stats(jerk_plan pl, int32_t item, double *h_mean, double *h_std, float *h_theta) {

@@ -14,6 +14,8 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libjerk.so")
+# the debug build with bounds checks in its kernels (see jerk_check_counts)
+LIB_CHECKS_PATH = os.path.join(_HERE, "_build_checks", "libjerk.so")
 
 JERK_OK, JERK_EINVAL, JERK_ENOMEM, JERK_ECUDA, JERK_ETIMEOUT, JERK_EOVERFLOW, JERK_ESTATE = range(7)
 THRESH_ABS, THRESH_SIGMA = 0, 1
@@ -24,7 +26,7 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
            "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits",
-           "jerk_measure_peaks")
+           "jerk_measure_peaks", "jerk_check_counts")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -70,10 +72,12 @@ def lib() -> ctypes.CDLL:
     """Load libjerk.so (built by ``paper_1911_01353_gb300.build``)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
+        checks = os.environ.get("JERK_CHECKS") == "1"
+        path = LIB_CHECKS_PATH if checks else LIB_PATH
+        if not os.path.exists(path):
             raise RuntimeError("libjerk.so is not built (%s); run "
-                               "`python -m paper_1911_01353_gb300.build`" % LIB_PATH)
-        L = ctypes.CDLL(LIB_PATH)
+                               "`python -m paper_1911_01353_gb300.build%s`" % (path, " --checks" if checks else ""))
+        L = ctypes.CDLL(path)
         vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
         st = ctypes.c_int
         sig = {
@@ -103,6 +107,7 @@ def lib() -> ctypes.CDLL:
                               st),
             "jerk_refine": ([vp, vp, i64, ctypes.POINTER(Candidate), i32, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(i32), ctypes.POINTER(Refined), vp], st),
+            "jerk_check_counts": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
             "jerk_check_waits": ([vp, i32, vp], st),
             "jerk_measure_peaks": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                    st),
@@ -312,6 +317,14 @@ class Plan:
         if code == JERK_EINVAL:
             _check(code, "jerk_check_waits")
         return code
+
+    def check_counts(self):
+        """(violations, first site, compiled in) of the debug build's bounds
+        checks (jerk_check_counts); waits for the plan's work."""
+        v, site, on = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().jerk_check_counts(self._h, ctypes.byref(v), ctypes.byref(site), ctypes.byref(on)),
+               "jerk_check_counts")
+        return int(v.value), int(site.value), bool(on.value)
 
     def stats(self, item: int = 0):
         k = int(self.params.n_stages)
