@@ -37,6 +37,17 @@ def test_library_exports_every_declared_function(L):
         assert hasattr(L, name), name
 
 
+def test_checked_build_compiles_and_exports_every_declared_function():
+    """The debug build (-DJERK_CHECKS, bounds checks in the kernels) compiles
+    from the same sources into its own library and exports the same ABI."""
+    from paper_1911_01353_gb300 import build
+    path = build.build(checks=True)
+    assert path == build.LIB_CHECKS and path != build.LIB
+    Lc = ctypes.CDLL(path)
+    for name in header_functions():
+        assert hasattr(Lc, name), name
+
+
 def test_status_strings(L):
     for code in range(7):
         s = L.jerk_status_str(code).decode()
