@@ -57,6 +57,9 @@ def args_():
     ap.add_argument("--autotune", action="store_true", help="pick the segment length by timing (cached)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seg-len", type=int, default=0)
+    ap.add_argument("--stages", default="",
+                    help="harmonic stages of the paper-scale search, e.g. 1 or 1,2,4 (default: the "
+                         "workload's 1,2,4,8)")
     ap.add_argument("--precision", type=int, default=0, choices=(0, 1, 2),
                     help="filter arithmetic: 0 FP32, 1 BF16 tensor-core DFT blocks, 2 FP16 tensor-core DFT blocks")
     ap.add_argument("--bins", type=int, default=1 << 22,
@@ -64,9 +67,16 @@ def args_():
     return ap.parse_args()
 
 
-def workload(name, bins=1 << 22):
+def workload(name, bins=1 << 22, stages=""):
+    import dataclasses
+
     import synth
-    return synth.paper_scale(bins) if name == "paper" else synth.small_single()
+    wl = synth.paper_scale(bins) if name == "paper" else synth.small_single()
+    if stages:
+        st = tuple(int(x) for x in stages.split(","))
+        wl = dataclasses.replace(wl, stages=st, thresh=tuple(wl.thresh[:len(st)]),
+                                 name=wl.name.replace("stages 1-2-4-8", "stages " + "-".join(map(str, st))))
+    return wl
 
 
 def peaks_file():
@@ -247,7 +257,7 @@ def tc_accuracy(wl, spec, plan, x, fp32_cands, tc_cands, cells=65536):
 
 def reference_arm(a):
     import synth  # noqa: F401
-    wl = workload(a.workload, a.bins)
+    wl = workload(a.workload, a.bins, a.stages)
     spec = wl.make()
     times, cells = [], 0
     per_step = max(0.5, min(6.0, 120.0 / max(1, a.warmup + a.steps)))   # the whole run: about 2 minutes
@@ -458,7 +468,7 @@ def main():
     torch.cuda.set_device(local)
 
     import synth
-    wl = workload(a.workload, a.bins)
+    wl = workload(a.workload, a.bins, a.stages)
     spec = synth.spectrum(wl.n_bins, wl.seed + 1000 * rank, wl.signals) if rank else wl.make()
     p = pkg.make_params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages,
                         thresh=SIGMA_T[:len(wl.stages)], thresh_mode=pkg.THRESH_SIGMA,
