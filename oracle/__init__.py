@@ -23,7 +23,13 @@ What it computes, in the order of the paper's pipeline (Adamek et al.,
 7. ``peaks``          thresholded peak finding on the max-projection over
                       (z, w) (Sec. 3 "peak-finding ... above some user
                       specified threshold"; the 1-D peak rule is a reading).
-8. ``power_at``       the filter response at any point (r, z, w) of the
+8. ``fft_search``     steps 3-7 for the whole bank by the FFT route:
+                      overlap-and-save with a radix-2 FP64 DFT (``dft``),
+                      one power row at a time, never the whole plane; the
+                      harmonic sums, max-projections (with the runner-up
+                      value per cell) and statistics accumulated as rows
+                      come.  For spectra too long for direct summation.
+9. ``power_at``       the filter response at any point (r, z, w) of the
                       continuous parameter space (the plane off its grid),
                       by direct summation with rho; ``refine`` takes its
                       maximum over a small grid around a candidate, and
@@ -74,6 +80,17 @@ def _load():
         lib.oracle_power_cells.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, lp, lp, lp,
                                            lp, ctypes.c_int64, dp]
         lib.oracle_threads.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.oracle_dft.argtypes = [dp, ctypes.c_int64, ctypes.c_int]
+        lib.oracle_dft.restype = ctypes.c_int
+        lib.oracle_fft_search.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, lp, lp, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_int, ip, lp, ip, lp, ctypes.c_int64,
+                                          lp, fp, ip, fp, dp, lp]
+        lib.oracle_fft_search.restype = ctypes.c_int
+        lib.oracle_fft_rows.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, lp, lp, ctypes.c_int64,
+                                        ctypes.c_int64, lp, ctypes.c_int64, dp]
+        lib.oracle_fft_rows.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -439,4 +456,118 @@ def search(F: np.ndarray, p: Params, bank: Bank | None = None, keep_plane: bool 
     if keep_plane:
         res.plane = P
         res.normalised = Fn
+    return res
+
+
+# ---------------------------------------------------------------------------
+# The FFT route: the whole search of a long spectrum, one row at a time
+# ---------------------------------------------------------------------------
+
+def dft(x, sign: int) -> np.ndarray:
+    """X_k = sum_j x_j exp(sign 2 pi i j k / n) by the oracle's radix-2 DFT
+    (n a power of two, unnormalised)."""
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.complex128)).copy()
+    if _load().oracle_dft(_dp(a.view(np.float64)), a.size, int(sign)) != 0:
+        raise ValueError("length must be a power of two")
+    return a
+
+
+def harmonic_table(p: Params):
+    """harm[t, h-1] = template index of (h z_t, h w_t) for h = 1..8 (-1 off
+    the grid); top[t] = number of stages at which t is a valid fundamental
+    (|H z_t| <= zmax and |H w_t| <= wmax; the sets are nested in H)."""
+    zt, wt = grid(p)
+    T = zt.size
+    harm = np.full((T, 8), -1, dtype=np.int64)
+    top = np.zeros(T, dtype=np.int32)
+    for t in range(T):
+        z, w = int(zt[t]), int(wt[t])
+        for h in range(1, 9):
+            hz, hw = h * z, h * w
+            if abs(hz) <= p.zmax and abs(hw) <= p.wmax:
+                harm[t, h - 1] = ((hw + p.wmax) // p.dw) * p.nz + (hz + p.zmax) // p.dz
+        top[t] = sum(1 for H in p.stages if abs(H * z) <= p.zmax and abs(H * w) <= p.wmax)
+    return harm, top
+
+
+def fft_rows(Fn: np.ndarray, p: Params, bank: Bank, templates, L: int = 8192) -> np.ndarray:
+    """Power rows P[t][p], p < b N, of the given templates by the FFT route
+    alone (overlap-and-save with the oracle's radix-2 DFT of length L)."""
+    Fn = np.ascontiguousarray(np.asarray(Fn, dtype=np.complex128))
+    tl = np.ascontiguousarray(np.asarray(templates, dtype=np.int64))
+    bN = p.numbetween * Fn.size
+    out = np.empty((tl.size, bN), dtype=np.float64)
+    rc = _load().oracle_fft_rows(_dp(Fn.view(np.float64)), Fn.size, p.numbetween,
+                                 _dp(bank.flat.view(np.float64)), _lp(bank.off), _lp(bank.D),
+                                 p.n_templates, int(L), _lp(tl), tl.size, _dp(out))
+    if rc != 0:
+        raise ValueError("oracle_fft_rows: bad sizes")
+    return out
+
+
+@dataclass
+class FftResult:
+    candidates: list = field(default_factory=list)   # (stage, p, t, power32)
+    maxproj: dict = field(default_factory=dict)      # H -> (M float32, argmax t)
+    runner_up: dict = field(default_factory=dict)    # H -> second-best FP32 value per cell
+    theta: dict = field(default_factory=dict)        # H -> float32
+    stats: dict = field(default_factory=dict)        # H -> (mu, sd)
+    rows: int = 0                                    # power rows computed
+
+
+def fft_search(Fn: np.ndarray, p: Params, bank: Bank | None = None, L: int = 8192,
+               fund=None) -> FftResult:
+    """Steps 3-7 of ``search`` for the normalised spectrum Fn by the FFT route.
+
+    Every power row P(., z_t, w_t) is computed by overlap-and-save with the
+    oracle's radix-2 FP64 DFT of length L; rows of the harmonics (h z, h w) of
+    a fundamental are computed when that fundamental is processed, so the
+    plane is never held.  With ``fund`` (ascending template indices) only
+    those fundamentals are processed (for timing; the statistics and
+    candidates then describe that subset).  Statistics: mu = E[S_H],
+    sd = (E[S_H^2] - mu^2)^(1/2) over the defined cells (population values,
+    FP64 sums)."""
+    Fn = np.ascontiguousarray(np.asarray(Fn, dtype=np.complex128))
+    harm, top = harmonic_table(p)
+    T = p.n_templates
+    if fund is None:
+        fund = np.arange(T, dtype=np.int64)
+    fund = np.ascontiguousarray(np.asarray(fund, dtype=np.int64))
+    if bank is None:
+        need = sorted({int(harm[t, h - 1]) for t in fund.tolist()
+                       for h in range(1, p.stages[top[t] - 1] + 1)})
+        bank = Bank(p, templates=need)
+    bN = p.numbetween * Fn.size
+    nv = [n_valid(bN, H) for H in p.stages]
+    moff = np.concatenate([[0], np.cumsum(nv)[:-1]]).astype(np.int64)
+    tot = int(sum(nv))
+    Mv = np.full(tot, -np.inf, dtype=np.float32)
+    M2 = np.full(tot, -np.inf, dtype=np.float32)
+    Mt = np.full(tot, -1, dtype=np.int32)
+    sums = np.zeros(2 * len(p.stages), dtype=np.float64)
+    st = np.ascontiguousarray(np.array(p.stages, dtype=np.int32))
+    rows = ctypes.c_int64(0)
+    ip = ctypes.POINTER(ctypes.c_int32)
+    fp = ctypes.POINTER(ctypes.c_float)
+    rc = _load().oracle_fft_search(
+        _dp(Fn.view(np.float64)), Fn.size, p.numbetween, _dp(bank.flat.view(np.float64)), _lp(bank.off),
+        _lp(bank.D), T, int(L), len(p.stages), st.ctypes.data_as(ip), _lp(np.ascontiguousarray(harm)),
+        top.ctypes.data_as(ip), _lp(fund), fund.size, _lp(moff), Mv.ctypes.data_as(fp),
+        Mt.ctypes.data_as(ip), M2.ctypes.data_as(fp), _dp(sums), ctypes.byref(rows))
+    if rc != 0:
+        raise ValueError("oracle_fft_search: bad sizes (L must be a power of two above the taps)")
+    res = FftResult(rows=int(rows.value))
+    for si, H in enumerate(p.stages):
+        a, n = int(moff[si]), nv[si]
+        M, arg, sec = Mv[a:a + n].copy(), Mt[a:a + n].astype(np.int64), M2[a:a + n].copy()
+        count = float(n) * float(sum(1 for t in fund.tolist() if top[t] > si))
+        mu = sums[2 * si] / count
+        sd = math.sqrt(max(0.0, sums[2 * si + 1] / count - mu * mu))
+        res.stats[H] = (mu, sd)
+        th = np.float32(p.thresh[si]) if p.thresh_mode == "abs" else np.float32(mu + p.thresh[si] * sd)
+        res.theta[H] = th
+        res.maxproj[H] = (M, arg)
+        res.runner_up[H] = sec
+        for c in peaks(M, th):
+            res.candidates.append((H, int(c), int(arg[c]), float(M[c])))
     return res

@@ -342,3 +342,128 @@ def test_is_peak3d_rules():
     assert oracle.is_peak3d(F, r0, z0, w0, 2, 2.0, 20.0)              # the signal's own cell
     assert not oracle.is_peak3d(F, r0 + 0.5, z0, w0, 2, 2.0, 20.0)    # a neighbour is higher
     assert not oracle.is_peak3d(F, r0, z0 + 2.0, w0, 2, 2.0, 20.0)
+
+
+# ---------------------------------------------------------------------------
+# The FFT route (overlap-and-save with the oracle's own radix-2 DFT)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 8, 1024, 8192])
+def test_dft_matches_library_fft(n):
+    """The oracle's radix-2 DFT against NumPy's FFT (an independent
+    implementation), both signs."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    scale = max(1.0, float(np.abs(np.fft.fft(x)).max()))
+    assert np.max(np.abs(oracle.dft(x, -1) - np.fft.fft(x))) <= 1e-13 * scale
+    assert np.max(np.abs(oracle.dft(x, +1) - np.fft.ifft(x) * n)) <= 1e-13 * scale
+    with pytest.raises(ValueError):
+        oracle.dft(np.ones(6), -1)
+
+
+@pytest.mark.parametrize("L", [512, 8192])
+def test_fft_route_rows_equal_direct_correlation(L):
+    """Every template of a 4096-bin case: the overlap-and-save rows equal the
+    direct correlation's |O_p|^2 at every cell to 1e-12 of the row maximum
+    (L = 512: 20+ segments with a ragged last one; L = 8192: one segment
+    longer than the spread spectrum)."""
+    wl = synth.Workload("t", 4096, 20, 2, 60, 20, (1,), (10.0,), 5,
+                        [synth.Signal(1000.25, 12.0, 40.0, 40.0, 0.3), synth.Signal(4090.5, -20.0, -60.0, 30.0, 1.0)])
+    p = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=(1,))
+    Fn = oracle.normalise(wl.make(), p.norm_block)
+    bank = oracle.Bank(p)
+    rows = oracle.fft_rows(Fn, p, bank, range(p.n_templates), L=L)
+    for t in range(p.n_templates):
+        o = oracle.correlate(Fn, bank.taps(t), p.numbetween)
+        want = o.real * o.real + o.imag * o.imag
+        assert np.max(np.abs(rows[t] - want)) <= 1e-12 * want.max(), t
+
+
+def test_fft_route_rejects_short_transform():
+    p = oracle.Params(20, 2, 60, 20, stages=(1,))
+    bank = oracle.Bank(p, templates=[0])
+    with pytest.raises(ValueError):
+        oracle.fft_rows(np.ones(64, np.complex64), p, bank, [0], L=64)      # L below 2 D + 1
+
+
+@pytest.mark.parametrize("mode,thresh,stages", [("abs", (15.0, 20.0), (1, 2)), ("sigma", (5.0, 5.0, 4.0), (1, 2, 3))])
+def test_fft_search_equals_direct_search(mode, thresh, stages):
+    """The whole search by the FFT route against ``search`` (direct
+    summation, the whole plane held): identical candidates, max-projections
+    and argmax (outside exact FP32 ties), runner-up values equal to the
+    second-largest FP32 harmonic sum per cell, statistics to 1e-12."""
+    wl = synth.small_single()
+    p = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=stages, thresh_mode=mode, thresh=thresh)
+    F = wl.make()
+    ref = oracle.search(F, p)
+    got = oracle.fft_search(oracle.normalise(F, p.norm_block), p, L=2048)
+    assert got.candidates == ref.candidates and len(ref.candidates) > 0
+    for H in stages:
+        M, arg = ref.maxproj[H]
+        fund, S = ref.sums[H]
+        S32 = np.sort(S.astype(np.float32), axis=0)
+        assert np.array_equal(got.maxproj[H][0], M)
+        assert np.array_equal(got.runner_up[H], S32[-2])
+        tie = S32[-1] == S32[-2]
+        assert np.array_equal(got.maxproj[H][1][~tie], arg[~tie])
+        for a, b in zip(got.stats[H], ref.stats[H]):
+            assert abs(a - b) <= 1e-12 * abs(b)
+        assert got.theta[H] == ref.theta[H]
+    assert got.rows == sum(max(h for h in stages if abs(h * z) <= p.zmax and abs(h * w) <= p.wmax)
+                           for z, w in zip(*oracle.grid(p)))
+
+
+def test_fft_search_reproduces_stored_direct_result():
+    """The stored direct-summation result of the 2^16-bin workload
+    (tests/golden/small_single_candidates.json, written by make_golden.py
+    from ``oracle.search``) is reproduced by the FFT route."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "small_single_candidates.json")
+    with open(path) as f:
+        g = json.load(f)
+    wl = synth.small_single()
+    q = g["params"]
+    p = oracle.Params(q["zmax"], q["dz"], q["wmax"], q["dw"], stages=tuple(q["stages"]),
+                      thresh_mode=q["thresh_mode"], thresh=tuple(q["thresh"]), norm_block=q["norm_block"])
+    got = oracle.fft_search(oracle.normalise(wl.make(), p.norm_block), p)
+    assert [list(c) for c in got.candidates] == g["candidates"]
+    for H, (mu, sd) in g["stats"].items():
+        assert abs(got.stats[int(H)][0] - mu) <= 1e-12 * mu
+        assert abs(got.stats[int(H)][1] - sd) <= 1e-12 * sd
+
+
+def test_fft_search_subset_of_fundamentals():
+    """Processing only some fundamentals gives the max over those alone."""
+    wl = synth.small_single()
+    p = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=(1,))
+    Fn = oracle.normalise(wl.make(), p.norm_block)
+    sub = [3, 40, 77, 146]
+    got = oracle.fft_search(Fn, p, fund=sub)
+    bank = oracle.Bank(p, templates=sub)
+    P = np.stack([np.abs(oracle.correlate(Fn, bank.taps(t), p.numbetween)) ** 2 for t in sub])
+    P32 = P.astype(np.float32)
+    assert np.array_equal(got.maxproj[1][0], P32.max(axis=0))
+    assert got.rows == len(sub)
+
+
+def test_power_cells_equal_correlate():
+    """Bank.power_cells (its own C loop with per-template offsets) equals
+    |correlate|^2 at random (t, p) over templates of different half-widths,
+    including cells at both ends of the spectrum."""
+    wl = synth.small_single()
+    p = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw)
+    Fn = oracle.normalise(wl.make(), p.norm_block)
+    bN = p.numbetween * Fn.size
+    picks = [0, 10, 44, 63, 73, 146]                    # m = 34, 24, 27, 26, 16, 34 bins
+    bank = oracle.Bank(p, templates=picks)
+    assert len({int(bank.D[t]) for t in picks}) >= 4
+    rng = np.random.default_rng(31)
+    ps = np.concatenate([[0, 1, 2, 5, bN - 3, bN - 2, bN - 1], rng.integers(0, bN, 200),
+                         [20000, 20001]])
+    full = {t: np.abs(oracle.correlate(Fn, bank.taps(t), p.numbetween)) ** 2 for t in picks}
+    tt = np.repeat(picks, ps.size)
+    pp = np.tile(ps, len(picks))
+    got = bank.power_cells(Fn, tt, pp)
+    want = np.array([full[int(t)][int(q)] for t, q in zip(tt, pp)])
+    assert np.max(np.abs(got - want)) <= 1e-13 * max(1.0, want.max())
