@@ -18,7 +18,10 @@
 // host threads on the same device) race on it and must be serialised by the
 // caller.  The device address of the array is looked up once per device, on
 // that device's first call (with the device current), so that first call
-// should be made before any CUDA stream capture starts.
+// should be made before any CUDA stream capture starts.  The address is kept
+// for the life of the process: after cudaDeviceReset on a device, this entry
+// point must not be called on that device again in the same process (the
+// kept address would no longer belong to the new context).
 #include <mutex>
 
 #include "jerk_internal.h"
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(unsigned long long *scratch,
 }
 
 struct GridArgs {
-    int32_t stage, zmax, dz, wmax, dw, nz;
+    int32_t stage, zmax, dz, wmax, dw, nz, T;   // T = nz * nw templates
 };
 
 // 3. write the records in cell order at the block's offset
@@ -154,12 +157,15 @@ __global__ void __launch_bounds__(kThreads) write_kernel(const unsigned long lon
         jerk_candidate rec;
         rec.p = p;
         rec.r = (double)p / 2.0;
+        // a cell that no template reached (or a stale value) decodes to a t
+        // outside the grid: reported as the library's candidates do
+        const bool on_grid = t >= 0 && t < g.T;
         rec.t = t;
-        rec.z_idx = t % g.nz;
-        rec.w_idx = t / g.nz;
+        rec.z_idx = on_grid ? t % g.nz : -1;
+        rec.w_idx = on_grid ? t / g.nz : -1;
         rec.stage = g.stage;
-        rec.z = (float)(-g.zmax + rec.z_idx * g.dz);
-        rec.w = (float)(-g.wmax + rec.w_idx * g.dw);
+        rec.z = on_grid ? (float)(-g.zmax + rec.z_idx * g.dz) : 0.f;
+        rec.w = on_grid ? (float)(-g.wmax + rec.w_idx * g.dw) : 0.f;
         rec.power = mval(x);
         rec.item = 0;
         out[k] = rec;
@@ -176,6 +182,7 @@ extern "C" jerk_status jerk_peaks_noalloc(const uint64_t *d_maxproj, int64_t n_c
     if (!d_maxproj || !d_count || n_cells < 1 || cap < 0 || (cap > 0 && !d_out)) return JERK_EINVAL;
     if (n_cells > kMaxCells) return JERK_EINVAL;   // beyond the fixed scratch array
     if (dz <= 0 || dw <= 0 || zmax < 0 || wmax < 0 || zmax % dz || wmax % dw || stage < 1) return JERK_EINVAL;
+    if ((int64_t)(2 * (int64_t)zmax / dz + 1) * (2 * (int64_t)wmax / dw + 1) > INT32_MAX) return JERK_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return JERK_ECUDA;
     unsigned long long *scratch = nullptr;
@@ -197,6 +204,7 @@ extern "C" jerk_status jerk_peaks_noalloc(const uint64_t *d_maxproj, int64_t n_c
     g.wmax = wmax;
     g.dw = dw;
     g.nz = 2 * zmax / dz + 1;
+    g.T = g.nz * (2 * wmax / dw + 1);
     const unsigned long long *M = (const unsigned long long *)d_maxproj;
     count_kernel<<<nblk, kThreads, 0, st>>>(M, n_cells, theta, scratch);
     scan_kernel<<<1, 1024, 0, st>>>(scratch, nblk, d_count);

@@ -88,3 +88,69 @@ def test_noalloc_rejects_oversize_and_reports_full_count(pkg):
         assert int(cnt.item()) == len(want) > 8
         got = _records(out, 8)
         assert [int(x) for x in got["p"]] == [c.p for c in want[:8]]
+
+
+def _numpy_peaks(packed: np.ndarray, theta: float):
+    """The library's peak rule on a packed max-projection, in NumPy: M(p) >
+    theta, M(p) > M(p-1), M(p) >= M(p+1), a missing neighbour as -inf."""
+    m = (packed >> np.uint64(32)).astype(np.uint32).view(np.float32).astype(np.float64)
+    left = np.concatenate([[-np.inf], m[:-1]])
+    right = np.concatenate([m[1:], [-np.inf]])
+    return np.nonzero((m > theta) & (m > left) & (m >= right))[0]
+
+
+def _pack(vals: np.ndarray, t: np.ndarray) -> np.ndarray:
+    hi = vals.astype(np.float32).view(np.uint32).astype(np.uint64) << np.uint64(32)
+    return hi | (np.uint64(0xFFFFFFFF) - t.astype(np.uint64))
+
+
+@pytest.mark.parametrize("n_cells,sparse", [((1 << 23) + 1234, False), (1 << 27, True)])
+def test_noalloc_large_synthetic_maxproj(pkg, n_cells, sparse):
+    """Sizes beyond one search of the small workload: 2^23 + 1234 cells (the
+    scan gives each of its threads several blocks, and the last block is
+    partial) and the largest accepted size, 2^27 cells.  A synthetic packed
+    array with planted peaks, some of them carrying a template index outside
+    the grid; count and records against the NumPy peak rule, two calls in a
+    row."""
+    from paper_1911_01353_gb300 import jerk
+    zmax, dz, wmax, dw = 20, 2, 60, 20
+    nz, T = 21, 147
+    rng = np.random.default_rng(n_cells)
+    if sparse:
+        vals = np.zeros(n_cells, dtype=np.float32)
+        t = np.zeros(n_cells, dtype=np.int64)
+    else:
+        vals = rng.uniform(0.0, 10.0, n_cells).astype(np.float32)
+        t = rng.integers(0, T, n_cells)
+    peaks = np.unique(np.concatenate([rng.integers(0, n_cells, 5000), [0, 1, n_cells - 2, n_cells - 1]]))
+    vals[peaks] = rng.uniform(20.0, 60.0, peaks.size).astype(np.float32)
+    vals[peaks[1::7]] = vals[np.minimum(peaks[1::7] + 1, n_cells - 1)]    # some plateaus
+    t[peaks] = rng.integers(0, T, peaks.size)
+    t[peaks[::11]] = T + 5                                                 # off the grid
+    packed = _pack(vals, t)
+    theta = 15.0
+    want = _numpy_peaks(packed, theta)
+    assert want.size > 1000
+    d = torch.from_numpy(packed.view(np.int64)).cuda()
+    cap = want.size + 16
+    for call in range(2):
+        out = torch.zeros(cap * jerk.CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        cnt = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+        jerk.peaks_noalloc(d.data_ptr(), n_cells, theta, 2, zmax, dz, wmax, dw, out.data_ptr(), cap,
+                           cnt.data_ptr())
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == want.size, call
+        got = _records(out, want.size)
+        assert np.array_equal(got["p"], want)
+        tw = t[want]
+        on = tw < T
+        assert np.array_equal(got["t"], tw)
+        assert np.array_equal(got["power"], vals[want])
+        assert np.array_equal(got["z_idx"][on], tw[on] % nz)
+        assert np.array_equal(got["w_idx"][on], tw[on] // nz)
+        assert np.all(got["z_idx"][~on] == -1) and np.all(got["w_idx"][~on] == -1)
+        assert np.all(got["z"][~on] == 0) and np.all(got["w"][~on] == 0)
+        assert np.array_equal(got["z"][on], (-zmax + (tw[on] % nz) * dz).astype(np.float32))
+        assert np.all(got["stage"] == 2) and np.array_equal(got["r"], want / 2.0)
+    del d
+    torch.cuda.empty_cache()
