@@ -36,8 +36,7 @@ METRIC = "template-bins/sec (f-fdot-fddot cells/s)"
 UNIT = "cells/s"
 SIGMA_T = (19.0, 17.0, 15.0, 14.0)
 FP32_LANES_PER_SM = 128
-SMS = 152
-SM_MAX_MHZ = 2070.0
+SM_MAX_MHZ_DEFAULT = 2070.0
 
 
 def args_():
@@ -102,15 +101,28 @@ def kernel_hash(main="conv.cu"):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(L, precision=0):
-    """DRAM bytes per launch of the fused kernel (FP32, or the tensor-core
-    kernel for precision 1/2) from the committed ncu summary, if it was taken
-    on the current kernel source; else None."""
-    name = "conv_paper_scale_traffic.txt" if precision == 0 else "conv_tc_paper_scale_traffic.txt"
+TRAFFIC_FILES = {0: "conv_kernel_traffic_2p16bins.txt", 1: "conv_tc_kernel_traffic_2p16bins.txt",
+                 2: "conv_tc_kernel_traffic_2p16bins.txt"}
+
+
+def conv_algorithmic_bytes(slot_floats, n_templates, L, n_bins):
+    """Bytes one filter launch must move: the harmonic rows it writes, the
+    template bank and the spectrum it reads, the stage-1 max-projection."""
+    return 4 * slot_floats + 8 * n_templates * L + 8 * n_bins + 8 * 2 * n_bins
+
+
+def recorded_traffic(L, alg_bytes, precision=0):
+    """DRAM bytes (read + write) per launch of the filter kernel (FP32, or the
+    tensor-core kernel for precision 1/2), from the committed ncu record of a
+    small case (one launch, 2^16 bins, the full bank: a few GB on the device),
+    scaled to this launch by the ratio of the two launches' algorithmic bytes
+    (``conv_algorithmic_bytes``).  Returns (bytes, note), or (None, why) when
+    no record was taken on the current kernel sources."""
+    name = TRAFFIC_FILES[precision]
     main = "conv.cu" if precision == 0 else "conv_tc.cu"
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
-        return None
+        return None, "no record"
     vals = {}
     with open(path) as f:
         for line in f:
@@ -118,11 +130,19 @@ def recorded_traffic(L, precision=0):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip()
     if vals.get("kernel_sha") != kernel_hash(main) or int(vals.get("seg_len", 0)) != L:
-        return None
+        return None, "record taken on other kernel sources"
+    if precision and int(vals.get("precision", 0)) != precision:
+        return None, "record taken at another precision"
     try:
-        return float(vals["dram_bytes_per_full_launch"])
+        small = float(vals["dram_bytes_per_launch"])
+        small_alg = float(vals["algorithmic_bytes_per_launch"])
+        bins = int(vals["bins"])
     except (KeyError, ValueError):
-        return None
+        return None, "malformed record"
+    return small * alg_bytes / small_alg, (
+        "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at %d bins (profiles/%s, "
+        "%.3f x its algorithmic bytes), scaled by algorithmic bytes (%.4g per launch here)"
+        % (bins, name, small / small_alg, alg_bytes))
 
 
 # ---------------------------------------------------------------------------
@@ -185,33 +205,38 @@ class ClockSampler:
 # CPU oracle (baseline leg and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_sample(wl, spec, seconds=12.0, stride=16, cells=65536):
-    """Time the FP64 oracle's direct correlation (plus the spectrum's
-    normalisation) on templates t = 0, stride, 2 stride, ... over `cells`
-    consecutive cells in the middle of the spectrum, until seconds elapses.
-    Returns (cells/s, cells done, threads, description)."""
+def oracle_sample(wl, spec, n_fund=1024):
+    """Time the FP64 oracle's FFT route (``oracle.fft_search``: normalisation,
+    forward DFTs of every segment, then per fundamental its own power row and
+    the rows of its harmonics, with the max-projections and statistics) on
+    n_fund fundamentals spread evenly over the bank.  The whole search needs
+    one row per (fundamental, harmonic) pair; the sample's time is scaled up
+    by rows.  Template taps are built first and not timed (plan time, like
+    the GPU's template bank).  Returns (cells/s, cells, threads, description,
+    seconds)."""
+    import numpy as np
+
     import oracle
-    op = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages)
-    zt, wt = oracle.grid(op)
-    p0 = wl.n_bins - cells // 2
-    t_start = time.perf_counter()
+    op = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages, thresh_mode="sigma",
+                       thresh=SIGMA_T[:len(wl.stages)])
+    T = op.n_templates
+    harm, top = oracle.harmonic_table(op)
+    rows_full = int(sum(op.stages[int(top[t]) - 1] for t in range(T)))
+    fund = np.unique(np.linspace(0, T - 1, min(n_fund, T)).astype(np.int64))
+    need = sorted({int(harm[t, h - 1]) for t in fund.tolist() for h in range(1, op.stages[int(top[t]) - 1] + 1)})
+    bank = oracle.Bank(op, templates=need)                      # taps: not timed
+    t0 = time.perf_counter()
     Fn = oracle.normalise(spec, op.norm_block)
-    done = 0
-    used = []
-    for t in range(0, op.n_templates, stride):
-        c = oracle.taps(int(zt[t]), int(wt[t]), op.numbetween, op.pad_bins)   # template (not timed below)
-        t0 = time.perf_counter()
-        o = oracle.correlate(Fn, c, op.numbetween, p0, cells)
-        _ = o.real * o.real + o.imag * o.imag
-        done += cells
-        used.append(time.perf_counter() - t0)
-        if time.perf_counter() - t_start > seconds:
-            break
-    corr_s = sum(used)
-    desc = ("FP64 direct correlation of the normalised spectrum with %d templates "
-            "(t = 0, %d, ...) over cells [%d, %d) of the %d-bin workload; template "
-            "build and normalisation not counted" % (len(used), stride, p0, p0 + cells, wl.n_bins))
-    return done / corr_s, done, oracle.threads(), desc
+    res = oracle.fft_search(Fn, op, bank=bank, fund=fund)
+    dt = time.perf_counter() - t0
+    cells_full = 2 * wl.n_bins * T
+    cells = cells_full * res.rows / rows_full                   # the sample's share of the search
+    desc = ("FP64 FFT route of the oracle (overlap-and-save, radix-2 DFT of length 8192) for %d of %d "
+            "fundamentals (evenly spaced): %d of the search's %d power rows, with harmonic sums, "
+            "max-projections and statistics, over the whole %d-bin spectrum; normalisation and segment "
+            "DFTs timed, template taps not; scaled to the whole search by rows"
+            % (fund.size, T, res.rows, rows_full, wl.n_bins))
+    return cells / dt, cells, oracle.threads(), desc, dt
 
 
 def tc_accuracy(wl, spec, plan, x, fp32_cands, tc_cands, cells=65536):
@@ -256,24 +281,29 @@ def tc_accuracy(wl, spec, plan, x, fp32_cands, tc_cands, cells=65536):
 
 
 def reference_arm(a):
-    import synth  # noqa: F401
+    """The oracle (there is no reference code: the reference is a paper) on
+    this arm's workload and metric: each step times its FFT route on a bounded
+    sample of fundamentals, sized so that the whole run takes about two
+    minutes."""
     wl = workload(a.workload, a.bins, a.stages)
     spec = wl.make()
-    times, cells = [], 0
-    per_step = max(0.5, min(6.0, 120.0 / max(1, a.warmup + a.steps)))   # the whole run: about 2 minutes
-    for i in range(a.warmup + a.steps):
-        t0 = time.perf_counter()
-        v, n, th, desc = oracle_sample(wl, spec, seconds=per_step, stride=97)
-        dt = time.perf_counter() - t0
+    steps = a.warmup + a.steps
+    # calibrate: rows per second of this host on a small sample
+    v, n, th, desc, dt = oracle_sample(wl, spec, n_fund=8)
+    per_step = max(1.0, 120.0 / max(1, steps))
+    n_fund = int(max(2, min(512, 8 * per_step / max(dt, 1e-3))))
+    times, cells = [], 0.0
+    for i in range(steps):
+        v, n, th, desc, dt = oracle_sample(wl, spec, n_fund=n_fund)
         if i >= a.warmup:
-            times.append(n / v)
+            times.append(dt)
             cells += n
     value = cells / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": wl.name, "sample": desc},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": th, "kind": "oracle FFT route", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -544,16 +574,20 @@ def main():
     e2e_value = world * cells * a.steps / (e2e_total / 1e3)
     conv_ms = statistics.mean(ph["conv"] for ph in phases)
     flops = conv_flops_per_cell(L, V) * cells
-    peak_alu = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12    # TFLOP/s, FP32 FMA
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_max_mhz = float(peaks_file()[0].get("sm_max_mhz") or SM_MAX_MHZ_DEFAULT)
+    peak_alu = sms * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12    # TFLOP/s, FP32 FMA
     achieved = flops / (conv_ms / 1e3) / 1e12
-    traffic = recorded_traffic(L, a.precision)
+    alg_bytes = conv_algorithmic_bytes(plan.info.slot_floats, plan.info.n_templates, L, wl.n_bins)
+    traffic, traffic_note = recorded_traffic(L, alg_bytes, a.precision)
     peaks, peaks_src = peaks_file()
 
     roof = {"bound": "alu", "kernel": "conv_kernel (fused FFT-multiply-IFFT-power)",
             "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-            "frac": achieved / peak_alu, "traffic": traffic,
+            "frac": achieved / peak_alu, "traffic": traffic, "traffic_note": traffic_note,
+            "algorithmic_bytes": alg_bytes,
             "flops_per_cell": conv_flops_per_cell(L, V),
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)",
+            "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (sms, sm_max_mhz),
             "measured": measured_peaks}
     # the second kernel of the step, bound by HBM: every harmonic row is read once
     # (the plan's row workspace, sized for this spectrum) and M_H written once
@@ -577,7 +611,7 @@ def main():
         roof = {"bound": "tensor", "kernel": "conv_tc_kernel (DFT blocks on tcgen05, %s operands)"
                                              % ("BF16" if a.precision == 1 else "FP16"),
                 "achieved": t_achieved, "peak": t_peak, "unit": "TFLOP/s", "frac": t_achieved / t_peak,
-                "traffic": traffic, "flops_per_cell": tflops_cell,
+                "traffic": traffic, "traffic_note": traffic_note, "flops_per_cell": tflops_cell,
                 "peak_source": "%s dense bf16 (sustained), FP16 at the same rate" % peaks_src,
                 "alu_view": {"achieved": achieved, "peak": peak_alu, "frac": achieved / peak_alu,
                              "note": "FP32-equivalent transform flops (5 L log2 L + 6 L + 3 V per segment)"}}
@@ -595,8 +629,9 @@ def main():
     if rank == 0:
         cpu = None
         if world == 1 and not a.no_cpu_baseline:
-            v, n, th, desc = oracle_sample(wl, spec)
-            cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle", "sample": desc}
+            v, n, th, desc, dt = oracle_sample(wl, spec)
+            cpu = {"value": v, "unit": UNIT, "cores": th, "kind": "oracle FFT route", "sample": desc,
+                   "seconds": round(dt, 2)}
         phase_mean = {k: round(statistics.mean(ph[k] for ph in phases), 4) for k in phases[0]}
         srt = sorted(step_ms)
         line = {

@@ -71,7 +71,8 @@ typedef struct {
     int32_t thresh_mode;     /* JERK_THRESH_ABS or JERK_THRESH_SIGMA */
     float   thresh[4];       /* ABS: power; SIGMA: T in theta = mu + T sigma */
     int32_t norm_block;      /* B in bins (1..4096), 0 = input already normalised */
-    int32_t precision;       /* 0 = FP32 (the only value accepted) */
+    int32_t precision;       /* filter arithmetic: 0 = FP32, 1 = BF16 and 2 = FP16 tensor-core
+                                DFT blocks (FP32 accumulation; seg_len 0 or 4096) */
     int64_t max_bins;        /* capacity: largest N a search may use (total over a batch), <= 2^29 */
     int64_t max_candidates;  /* capacity of the plan's candidate buffer (total over a batch) */
     int32_t max_batch;       /* largest number of spectra in one jerk_search_batch; 0 = 1 */
@@ -119,6 +120,11 @@ typedef struct {
     int64_t bank_bytes;      /* device bytes of the template bank and its tables, shared by
                                 every plan made from it with jerk_plan_share */
 } jerk_info;
+
+/* Check a parameter set without touching any GPU: JERK_OK if
+ * jerk_plan_create would accept it (device and memory aside), else
+ * JERK_EINVAL.  The rules are those stated on the fields of jerk_params. */
+jerk_status jerk_params_validate(const jerk_params *params);
 
 /* Validate `params`, select device `device` (made current), size and
  * allocate the plan's device memory for spectra of up to max_bins bins.
@@ -181,6 +187,49 @@ jerk_status jerk_search_batch(jerk_plan plan, const void *const *d_specs, const 
  * previous search only).  The two flags exclude each other. */
 jerk_status jerk_search_batch_grid(jerk_plan plan, const void *const *d_specs, const int64_t *n, const int32_t *zmax,
                                    const int32_t *wmax, int32_t count, int32_t flags, void *stream);
+
+/* ---- one search split over several GPUs by template range ----
+ *
+ * (No counterpart in the paper, which runs on one GPU.)  The max-projection
+ * of stage H is a maximum over fundamentals and the statistics are sums over
+ * them (Sec. 3), so one search divides exactly among ranks that each take a
+ * range of templates, followed by one max-reduction of the max-projections
+ * and one sum-reduction of the statistics:
+ *   1. every rank: jerk_search_range over its range (ranges partition
+ *      [0, n_templates)), then jerk_range_sums;
+ *   2. the caller reduces, over the ranks, each stage's max-projection
+ *      (jerk_maxproj; element-wise maximum of the packed uint64 entries, which
+ *      keeps the largest power and, on equal powers, the lowest t) and the
+ *      three sums (element-wise sum), writing the reduced arrays back in place;
+ *   3. jerk_select with the reduced sums; jerk_candidates then returns the
+ *      candidates of the whole search (all ranks may do this, or one).
+ * Merged max-projections equal those of jerk_search bitwise; the statistics
+ * differ from it only by the order of FP64 additions. */
+
+/* Partial search of d_spec (complex64[n], device) over the templates
+ * t_lo <= t < t_hi: the stage-1 max-projection over those templates, the
+ * stage-H max-projections over the fundamentals among them (their harmonic
+ * rows are made here even when the harmonic template lies outside the
+ * range), and the statistics of both (SIGMA mode).  No candidates are
+ * selected (jerk_candidates returns JERK_ESTATE until jerk_select).  Single
+ * spectrum (item 0).  Enqueued on `stream`. */
+jerk_status jerk_search_range(jerk_plan plan, const void *d_spec, int64_t n, int32_t t_lo, int32_t t_hi,
+                              void *stream);
+
+/* After jerk_search_range (synchronises it): per stage, the sum of S_H and
+ * of S_H^2 over the range's cells (SIGMA mode; 0 in ABS mode) and the number
+ * of cells counted.  Arrays of n_stages entries; any may be NULL.
+ * JERK_ESTATE unless the plan's last search was a jerk_search_range. */
+jerk_status jerk_range_sums(jerk_plan plan, double *h_sum, double *h_sumsq, double *h_count);
+
+/* Thresholds from the given (reduced) sums -- mu = sum/count,
+ * sd = (sumsq/count - mu^2)^(1/2), theta = mu + T sd in SIGMA mode, the
+ * given power in ABS mode (the arrays may then be NULL) -- and the peaks of
+ * the plan's current max-projections (Sec. 3), after the plan's previous
+ * work; synchronises.  jerk_stats and jerk_candidates then report them.
+ * Needs a single-spectrum search (jerk_search or jerk_search_range). */
+jerk_status jerk_select(jerk_plan plan, const double *h_sum, const double *h_sumsq, const double *h_count,
+                        void *stream);
 
 /* (No counterpart in the paper, which searches one spectrum at a time.)
  * A new plan that uses `parent`'s template bank (not copied; jerk_templates
@@ -273,7 +322,12 @@ jerk_status jerk_plan_info(jerk_plan plan, jerk_info *info);
 
 /* Where template t (0 <= t < n_templates) sits in the bank: *row is its row
  * of d_bank, *tap_offset the offset bM_g of its group (the spectrum of row
- * `row` is (1/L) sum_m c_{m - bM_g} exp(+2 pi i f m / L), m < 2 bM_g + 1) and
+ * `row` is G[f] = (1/L) sum_m c_{m - bM_g} exp(+2 pi i f m / L), m < 2 bM_g + 1,
+ * stored as such for precision 1 and 2; for precision 0 the row holds
+ * G[f] + G[f + L/2] at f < L/2 and (G[f - L/2] - G[f]) exp(+2 pi i k / R0) at
+ * f >= L/2, with R0 = 2^(log2 L mod 4) (16 if that is 1) and
+ * k = floor(floor((f - L/2) / (L/16)) / (16/R0)): the FP32 filter's folded
+ * form, because the spread spectrum's segments have period L/2) and
  * *seg_valid its group's segment length V_g = L - 2 bM_g.  Any output may be
  * NULL.  Templates are grouped by half-width m(z, w) so that a group of short
  * filters uses a short overlap. */
@@ -326,6 +380,27 @@ jerk_status jerk_profile(jerk_plan plan, int32_t enable);
  * JERK_ESTATE if the last search was not profiled. */
 jerk_status jerk_phase_times(jerk_plan plan, float *h_ms, int32_t n);
 
+/* ---- the harmonic sum indexed by the highest harmonic ----
+ *
+ * Sec. 3 names the harmonic sum without defining it; the main path sums
+ * over fundamentals (S_H above).  This is the other common form: for a top
+ * harmonic at cell q of template t = (z, w),
+ *   S'_H(q, t) = sum_{h=1..H} P(round(h q / H), z_h, w_h),
+ * (z_h, w_h) = the grid point nearest to (h z / H, h w / H), halves rounded
+ * away from zero in q, z and w; every template and every cell is a top
+ * harmonic.  It needs the whole power plane, so it serves banks whose plane
+ * fits on the device.  d_plane: float32[n_templates][b n] (device), the
+ * planes of jerk_plane for t0 = 0, nt = n_templates.  Writes, for stage H
+ * (1..8), d_maxproj (uint64[b n], device): the max over t of S'_H(q, t) in the
+ * packed form of jerk_maxproj (FP32 sums in h order, lowest t on equal
+ * values), and d_sums (double[2], device): the sum of S'_H and of S'_H^2 over
+ * all templates and cells (for mu = d_sums[0] / (n_templates b n) etc.).
+ * Thresholds and peaks: jerk_peaks_noalloc on d_maxproj.  Enqueued on
+ * `stream` after the plan's previous work; uses the plan's statistics
+ * workspace, so it must not overlap another call on the same plan. */
+jerk_status jerk_subharmonic(jerk_plan plan, const float *d_plane, int64_t n, int32_t H, uint64_t *d_maxproj,
+                             double *d_sums, void *stream);
+
 /* ---- candidate extraction without allocation (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory at the point where they
@@ -346,7 +421,11 @@ jerk_status jerk_phase_times(jerk_plan plan, float *h_ms, int32_t n);
  * JERK_EINVAL.  All calls share that array: calls that may overlap on a GPU
  * (other streams or host threads) race and must be serialised by the caller.
  * The first call on a device looks up the array's device address with that
- * device current; make it before starting any CUDA stream capture.
+ * device current; make it before starting any CUDA stream capture.  The
+ * address is kept for the life of the process, so after cudaDeviceReset on a
+ * device this call must not be used on that device again.  A cell whose
+ * packed template index lies outside the grid (no template reached it) gets
+ * z_idx = w_idx = -1 and z = w = 0, as in jerk_candidates.
  * Enqueued on `stream` on the current device; no host synchronisation. */
 jerk_status jerk_peaks_noalloc(const uint64_t *d_maxproj, int64_t n_cells, float theta, int32_t stage,
                                int32_t zmax, int32_t dz, int32_t wmax, int32_t dw,

@@ -512,6 +512,7 @@ class FftResult:
     runner_up: dict = field(default_factory=dict)    # H -> second-best FP32 value per cell
     theta: dict = field(default_factory=dict)        # H -> float32
     stats: dict = field(default_factory=dict)        # H -> (mu, sd)
+    sums: dict = field(default_factory=dict)         # H -> (sum S_H, sum S_H^2, cells counted)
     rows: int = 0                                    # power rows computed
 
 
@@ -561,13 +562,78 @@ def fft_search(Fn: np.ndarray, p: Params, bank: Bank | None = None, L: int = 819
         a, n = int(moff[si]), nv[si]
         M, arg, sec = Mv[a:a + n].copy(), Mt[a:a + n].astype(np.int64), M2[a:a + n].copy()
         count = float(n) * float(sum(1 for t in fund.tolist() if top[t] > si))
-        mu = sums[2 * si] / count
-        sd = math.sqrt(max(0.0, sums[2 * si + 1] / count - mu * mu))
+        res.sums[H] = (float(sums[2 * si]), float(sums[2 * si + 1]), count)
+        mu = sums[2 * si] / count if count > 0 else 0.0
+        sd = math.sqrt(max(0.0, sums[2 * si + 1] / count - mu * mu)) if count > 0 else 0.0
         res.stats[H] = (mu, sd)
         th = np.float32(p.thresh[si]) if p.thresh_mode == "abs" else np.float32(mu + p.thresh[si] * sd)
         res.theta[H] = th
         res.maxproj[H] = (M, arg)
         res.runner_up[H] = sec
+        for c in peaks(M, th):
+            res.candidates.append((H, int(c), int(arg[c]), float(M[c])))
+    return res
+
+
+# ---------------------------------------------------------------------------
+# The harmonic sum indexed by the highest harmonic (sub-harmonic form)
+# ---------------------------------------------------------------------------
+
+def round_ratio(a, h: int, H: int):
+    """Nearest integer to a h / H, halves rounded away from zero (integer
+    arithmetic; a may be an array of any sign)."""
+    a = np.asarray(a, dtype=np.int64)
+    m = np.abs(a) * h
+    q = (2 * m + H) // (2 * H)
+    return np.sign(a) * q
+
+
+def subharmonic_templates(p: Params, H: int) -> np.ndarray:
+    """sub[t, h-1] = template index of (z_h, w_h), the grid point nearest to
+    (h z_t / H, h w_t / H) for h = 1..H (reading: the sub-harmonic terms of a
+    top harmonic at (z_t, w_t), rounded on the grid, halves away from zero)."""
+    zt, wt = grid(p)
+    zi = zt // p.dz
+    wi = wt // p.dw
+    sub = np.empty((zt.size, H), dtype=np.int64)
+    for h in range(1, H + 1):
+        zh = round_ratio(zi, h, H)
+        wh = round_ratio(wi, h, H)
+        sub[:, h - 1] = (wh + p.wmax // p.dw) * p.nz + (zh + p.zmax // p.dz)
+    return sub
+
+
+def subharmonic_sums(P: np.ndarray, p: Params, H: int) -> np.ndarray:
+    """S'_H[t, q] = sum_{h=1..H} P[t_h, round(h q / H)] for every template t
+    (the top harmonic) and every cell q < b N, FP64 in h order: the harmonic
+    sum of a signal whose H-th harmonic sits at (q, z_t, w_t) (the form of
+    Ransom's harmonic summing that the paper's method lineage uses, Sec. 3
+    names the harmonic sum; the rounding is a reading)."""
+    sub = subharmonic_templates(p, H)
+    q = np.arange(P.shape[1], dtype=np.int64)
+    S = np.zeros(P.shape, dtype=np.float64)
+    for h in range(1, H + 1):
+        S += P[sub[:, h - 1]][:, round_ratio(q, h, H)]
+    return S
+
+
+def subharmonic_search(F: np.ndarray, p: Params, bank: Bank | None = None):
+    """The whole path with the sub-harmonic form of every stage: plane,
+    S'_H over all templates and cells, statistics, max-projection over
+    (z, w) (FP32 decisions, lowest t on ties), thresholds and peaks.
+    Returns a Result (sums[H] = (all templates, S'_H))."""
+    Fn = normalise(F, p.norm_block)
+    P = plane(Fn, p, bank)
+    res = Result()
+    allt = np.arange(p.n_templates, dtype=np.int64)
+    for si, H in enumerate(p.stages):
+        S = P if H == 1 else subharmonic_sums(P, p, H)
+        res.stats[H] = stats(S)
+        th = threshold(p, si, S)
+        M, arg = maxproj(allt, S)
+        res.maxproj[H] = (M, arg)
+        res.theta[H] = th
+        res.sums[H] = (allt, S)
         for c in peaks(M, th):
             res.candidates.append((H, int(c), int(arg[c]), float(M[c])))
     return res

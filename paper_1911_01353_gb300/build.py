@@ -25,7 +25,8 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libjerk.so")
 OUT_CHECKS = os.path.join(HERE, "_build_checks")
 LIB_CHECKS = os.path.join(OUT_CHECKS, "libjerk.so")
-SOURCES = ["plan.cu", "templates.cu", "conv.cu", "conv_tc.cu", "kernels.cu", "noalloc.cu", "refine.cu"]
+SOURCES = ["plan.cu", "templates.cu", "conv.cu", "conv_tc.cu", "kernels.cu", "noalloc.cu", "refine.cu",
+           "subharmonic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(ROOT, "include")]

@@ -10,7 +10,11 @@
 //      TMA bulk copy (cp.async.bulk + mbarrier) issued during the previous
 //      template's transform and shared by the SEGS segments; pointwise
 //      multiply, inverse FFT in registers and padded shared memory, drop the
-//      K-1 overlap, |.|^2;
+//      K-1 overlap, |.|^2.  The bank holds each template in a folded form
+//      (sums and twiddled differences of its two spectrum halves): the
+//      segment's spectrum repeats with period L/2, so the transform's first
+//      pass splits into two half-size DFTs and each thread keeps only 8
+//      spectrum values;
 //   3. epilogue in registers: running (max, argmax) per cell over the group
 //      -> one packed 64-bit atomicMax per cell into the stage-1
 //      max-projection; statistics (SIGMA mode); the harmonic rows the
@@ -214,10 +218,12 @@ conv_kernel(ConvArgs a) {
         for (int r = 0; r < 16; ++r) work[rv + NT * r] = v[r];
         bar_half();
     }
-    // each thread keeps the 16 spectrum values it multiplies: X[j + NT m]
-    float2 xr[16];
+    // each thread keeps the spectrum values it multiplies: X[j + NT m] for
+    // m < 8 (the spread segment has zeros at its odd samples, so X has
+    // period L/2 = 8 NT and X[j + NT (m + 8)] = X[j + NT m])
+    float2 xr[8];
 #pragma unroll
-    for (int m = 0; m < 16; ++m) xr[m] = work[j + NT * m];
+    for (int m = 0; m < 8; ++m) xr[m] = work[j + NT * m];
 
     // ---- 2. templates of this group -----------------------------------------
     const auto twi = make_tw<LOG2L, +1>(twtab, j);
@@ -258,15 +264,11 @@ conv_kernel(ConvArgs a) {
         // A thread whose wait expired reads a buffer that may still be landing;
         // its values are discarded: the whole segment leaves at the barrier below.
         const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(it / NBUF) & 1u);
-        // products in the order pass 0's first radix-4 stage consumes them
+        // products with the folded template (sums for m < 8, twiddled
+        // differences for m >= 8), then pass 0 as two half-size DFTs
 #pragma unroll
-        for (int m1 = 0; m1 < 4; ++m1)
-#pragma unroll
-            for (int m2 = 0; m2 < 4; ++m2) {
-                const int m = m1 + 4 * m2;
-                v[m] = cmul(xr[m], tsm[j + NT * m]);
-            }
-        fft_pass0<LOG2L, +1>(v, twi);
+        for (int m = 0; m < 16; ++m) v[m] = cmul(xr[m & 7], tsm[j + NT * m]);
+        fft_pass0_folded<LOG2L, +1>(v, twi);
         // One barrier per template over the segment's threads: it reports an
         // expired wait, ends this segment's reads of the buffer, and orders the
         // previous template's reads of `work` and `stage` before their reuse.
@@ -440,6 +442,8 @@ conv_kernel(ConvArgs a) {
 #undef itm
 
 int conv_segs_per_cta(int log2L) { return log2L >= 13 ? 1 : 2; }
+
+int conv_fold_radix(int log2L) { return (log2L % 4) ? (1 << (log2L % 4)) : 16; }
 
 template <int LOG2L, int MODE, bool STATS, bool ROWS = false>
 static cudaError_t launch_one(const ConvArgs &a, int n_ctas, cudaStream_t st) {

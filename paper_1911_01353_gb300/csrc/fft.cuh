@@ -131,7 +131,9 @@ __device__ __forceinline__ void dft8(float2 (&a)[8]) {
 
 template <int SIGN, int R>
 __device__ __forceinline__ void dft_small(float2 (&b)[R]) {
-    if constexpr (R == 2) {
+    if constexpr (R == 1) {
+        // one point: its own transform
+    } else if constexpr (R == 2) {
         dft2<SIGN>(b[0], b[1]);
     } else if constexpr (R == 4) {
         dft4<SIGN>(b[0], b[1], b[2], b[3]);
@@ -292,6 +294,40 @@ __device__ __forceinline__ void fft_pass0(float2 (&a)[16], const Tw &tw) {
 #pragma unroll
         for (int k = 0; k < R0; ++k) b[k] = a[i + I0 * k];
         dft_small<SIGN, R0>(b);
+        tw.template apply0<R0>(b, i);
+#pragma unroll
+        for (int r = 0; r < R0; ++r) a[i + I0 * r] = b[r];
+    }
+}
+
+// Pass 0 of a transform whose input is a product X[f] G[f] with X of period
+// L/2 (the spectrum of a segment with zeros at every odd sample), from the
+// folded template of template_fft_kernel: a[m] for m < 8 holds X Ge (the sums
+// G[f] + G[f + L/2]) and a[m + 8] holds X Go (the twiddled differences), f =
+// j + NT m.  The radix-R0 DFT of each item then splits into two DFTs of R0/2
+// points whose outputs are the even and the odd outputs of the full one:
+// same results as fft_pass0 on the unfolded product, R0/2 fewer butterflies.
+template <int LOG2L, int SIGN, class Tw>
+__device__ __forceinline__ void fft_pass0_folded(float2 (&a)[16], const Tw &tw) {
+    using C = FftCfg<LOG2L>;
+    constexpr int R0 = C::R0, I0 = C::I0, RH = R0 / 2;
+    static_assert(I0 * RH == 8, "the folded halves are a[0..7] and a[8..15]");
+#pragma unroll
+    for (int i = 0; i < I0; ++i) {
+        float2 e[RH], o[RH];
+#pragma unroll
+        for (int k = 0; k < RH; ++k) {
+            e[k] = a[i + I0 * k];
+            o[k] = a[8 + i + I0 * k];
+        }
+        dft_small<SIGN, RH>(e);
+        dft_small<SIGN, RH>(o);
+        float2 b[R0];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            b[2 * r] = e[r];
+            b[2 * r + 1] = o[r];
+        }
         tw.template apply0<R0>(b, i);
 #pragma unroll
         for (int r = 0; r < R0; ++r) a[i + I0 * r] = b[r];

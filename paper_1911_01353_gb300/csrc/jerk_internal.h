@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <memory>
 #include <vector>
@@ -134,22 +135,25 @@ cudaError_t launch_normalise(const float2 *in, float2 *out, int64_t n, int block
 cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, const int32_t *tlist, int32_t t0, int32_t nt, int b,
                         int pad, int bM, const double2 *gl, int n_gl, double2 *out, cudaStream_t st);
 cudaError_t launch_template_fft(const double2 *taps, const int32_t *shift, const int32_t *klen, int32_t nt, int K,
-                                int L, const double2 *tw, float2 *bank, cudaStream_t st);
+                                int L, const double2 *tw, int fold_r0, float2 *bank, cudaStream_t st);
+int conv_fold_radix(int log2L);      // radix of the FP32 filter's first inverse pass (the bank's folded form)
 cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st);
 cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
 cudaError_t launch_conv_tc(int precision, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
-cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, cudaStream_t st);
+cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, int sms, cudaStream_t st);
 int conv_segs_per_cta(int log2L);
 cudaError_t launch_harmonic(const HarmArgs &a, int nblk_y, bool stats, cudaStream_t st);
 int harmonic_cells_per_block();
 cudaError_t launch_finalise_stats(const double *part1, int64_t n1, const double *partH, int64_t nH,
                                   int n_stages, const double *counts, const float *thresh, int mode,
                                   double *stats_out, float *theta_out, cudaStream_t st);
-cudaError_t launch_peaks(const PeakArgs &a, cudaStream_t st);
+cudaError_t launch_peaks(const PeakArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_wait_check(int *err, uint64_t limit_ns, cudaStream_t st);
 cudaError_t measure_peaks(int sms, double *fp32_tflops, double *l2_gbs);
 
 // host helpers
+int device_sms(int device);         // multiprocessor count of `device` (1 if the query fails)
+int current_device_sms();           // the same for the current device
 void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 
 }  // namespace jerk
@@ -158,6 +162,9 @@ void gauss_legendre(int n, std::vector<double> &x, std::vector<double> &w);
 struct BatchLayout {
     std::vector<int64_t> n;                        // lengths: the cache key
     std::vector<int32_t> zmax, wmax;               // per-item sub-grids (empty: whole bank); part of the key
+    int32_t t_lo = 0, t_hi = -1;                   // template range of a partial search (t_hi < 0: none); key
+    int64_t stat_ctas = -1;                        // range search: conv CTAs whose statistics count (>= 0)
+    std::vector<double> counts_host;               // [count][JERK_MAX_STAGES] cells counted by the statistics
     std::vector<int32_t> n_fund;                   // [count] fundamentals of each item (stages > 1)
     int64_t total_ctas = 0;
     int n_work = 0;
@@ -205,6 +212,7 @@ struct TransientTables {
 struct jerk_plan_s {
     jerk_params prm;
     int device;
+    int sms = 1;                       // streaming multiprocessors of the device (grid sizing)
     int b, nz, nw, T, M, K, L, log2L, V;
     std::vector<int32_t> zt, wt, mt;   // grid values and per-template half-width
     // device memory; the bank-level arrays belong to `share`
@@ -254,6 +262,7 @@ struct jerk_plan_s {
     // state
     int32_t last_count = 0;            // spectra of the last search
     bool searched = false;
+    bool partial = false;              // the last search was a jerk_search_range (no candidates yet)
     cudaEvent_t done = nullptr;
     bool profile = false, profiled = false;
     cudaEvent_t ev[JERK_N_PHASES + 1] = {};

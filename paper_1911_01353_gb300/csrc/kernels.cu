@@ -442,11 +442,11 @@ __global__ void peaks_kernel(PeakArgs a) {
     }
 }
 
-cudaError_t launch_peaks(const PeakArgs &a, cudaStream_t st) {
+cudaError_t launch_peaks(const PeakArgs &a, int sms, cudaStream_t st) {
     int64_t nmax = 0;
     for (int si = 0; si < a.n_stages; ++si) nmax = a.n_cells[si] > nmax ? a.n_cells[si] : nmax;
     int64_t nblk = (nmax + 255) / 256;
-    if (nblk > 152 * 16) nblk = 152 * 16;
+    if (nblk > (int64_t)sms * 16) nblk = (int64_t)sms * 16;
     if (nblk < 1) nblk = 1;
     dim3 grid((unsigned)nblk, (unsigned)a.n_stages);
     peaks_kernel<<<grid, 256, 0, st>>>(a);
@@ -506,6 +506,18 @@ __global__ void __launch_bounds__(256) l2_read_kernel(const float4 *__restrict__
             acc.w += v.w;
         }
     if (acc.x + acc.y + acc.z + acc.w == 12345.678f) out[threadIdx.x] = acc.x;
+}
+
+int device_sms(int device) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || n < 1) return 1;
+    return n;
+}
+
+int current_device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    return device_sms(dev);
 }
 
 cudaError_t measure_peaks(int sms, double *fp32_tflops, double *l2_gbs) {

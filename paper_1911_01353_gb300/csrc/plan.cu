@@ -33,7 +33,6 @@ BankShare::~BankShare() {
 
 namespace {
 
-constexpr int kSMs = 152;
 constexpr size_t kGroupBytes = 32u << 20;   // bank slice a template group keeps in L2
 
 jerk_status from_cuda(cudaError_t e) {
@@ -119,7 +118,7 @@ bool valid_in(const jerk_plan_s *pl, int t, int H, int zs, int ws) {
 // skips it).  *nf receives the fundamentals written to `fund`, nf_stage[si]
 // those valid at stage si.
 int64_t item_rows(const jerk_plan_s *pl, int64_t n, int zs, int ws, int64_t base, int64_t *soff, int64_t *slen,
-                  FundEntry *fund, int *nf, int64_t *nf_stage) {
+                  FundEntry *fund, int *nf, int64_t *nf_stage, int32_t t_lo = 0, int32_t t_hi = INT32_MAX) {
     const int64_t bN = (int64_t)pl->b * n;
     int64_t off = base;
     int k = 0;
@@ -128,6 +127,7 @@ int64_t item_rows(const jerk_plan_s *pl, int64_t n, int zs, int ws, int64_t base
         int top = 0;
         for (int si = 1; si <= pl->fund_top[f]; ++si)
             if (valid_in(pl, t, pl->prm.stages[si], zs, ws)) top = si;
+        if (t < t_lo || t >= t_hi) top = 0;           // a partial search's fundamentals: its range
         const int Hmaster = pl->prm.stages[pl->fund_top[f]];
         const int Htop = top ? pl->prm.stages[top] : 0;
         FundEntry fe;
@@ -163,7 +163,7 @@ int nseg_for(const jerk_plan_s *pl, int64_t n) {
 }
 
 int tpg_for(const jerk_plan_s *pl, int nseg, int nt) {
-    const int64_t target = (int64_t)kSMs * 6;
+    const int64_t target = (int64_t)pl->sms * 6;
     int64_t tpg = ((int64_t)nt * nseg + target - 1) / target;
     const int64_t cap = std::max<int64_t>(1, (int64_t)(kGroupBytes / ((size_t)pl->L * sizeof(float2))));
     tpg = std::min<int64_t>(std::max<int64_t>(tpg, 8), cap);
@@ -323,14 +323,27 @@ struct HostTables {
 
 // Launch tables for spectra of lengths n, item i searched over |z| <= zm[i],
 // |w| <= wm[i] (zm, wm empty: the whole bank).  Fills L's host fields and h.
+//
+// With t_hi >= 0 (one spectrum only) the tables are those of a partial search
+// over the templates t_lo <= t < t_hi: its stage-1 templates are those of the
+// range and its fundamentals (stages > 1) those of the range, whose harmonic
+// rows are made by templates inside or outside it.  The conv work lists the
+// range's templates of every group first, then the other templates that make
+// one of those rows; only the first part's CTAs count in the statistics.
 jerk_status plan_tables(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n,
-                        const std::vector<int32_t> &zm, const std::vector<int32_t> &wm, HostTables &h) {
+                        const std::vector<int32_t> &zm, const std::vector<int32_t> &wm, HostTables &h,
+                        int32_t t_lo = 0, int32_t t_hi = -1) {
     const int count = (int)n.size();
     const int ns = pl->prm.n_stages;
-    const bool sub = !zm.empty();
+    const bool range = t_hi >= 0;
+    const bool sub = !zm.empty() || range;
+    if (range && (count != 1 || !zm.empty() || t_lo < 0 || t_hi > pl->T || t_lo >= t_hi)) return JERK_EINVAL;
     L.n = n;
     L.zmax = zm;
     L.wmax = wm;
+    L.t_lo = t_lo;
+    L.t_hi = t_hi;
+    L.stat_ctas = -1;
     L.total_ctas = 0;
     L.item_cta0.assign(count + 1, 0);
     L.harm0.assign(count + 1, 0);
@@ -349,7 +362,7 @@ jerk_status plan_tables(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64
     int64_t spec = 0, m[JERK_MAX_STAGES] = {0, 0, 0, 0};
     const int segs = conv_segs_per_cta(pl->log2L);
     for (int i = 0; i < count; ++i) {
-        const int zs = sub ? zm[i] : pl->prm.zmax, ws = sub ? wm[i] : pl->prm.wmax;
+        const int zs = !zm.empty() ? zm[i] : pl->prm.zmax, ws = !zm.empty() ? wm[i] : pl->prm.wmax;
         const int64_t bN = (int64_t)pl->b * n[i];
         L.spec_off[i] = spec;
         spec += n[i];
@@ -361,31 +374,47 @@ jerk_status plan_tables(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64
         int nf = 0;
         const int64_t used = item_rows(pl, n[i], zs, ws, L.slot_base[i], h.soff.data() + (size_t)i * pl->n_entries,
                                        h.slen.data() + (size_t)i * pl->n_entries,
-                                       h.fund.data() + (size_t)i * pl->n_fund, &nf, nf_stage);
+                                       h.fund.data() + (size_t)i * pl->n_fund, &nf, nf_stage,
+                                       range ? t_lo : 0, range ? t_hi : INT32_MAX);
         L.slot_base[i + 1] = L.slot_base[i] + used;
         L.n_fund[i] = nf;
         // conv work: this spectrum's (group, segment range) entries, item-major;
         // a sub-grid keeps, per group, the templates inside it (positions into `rows`)
         int64_t nt_item = 0;
-        for (const auto &g : pl->groups) {
-            ConvGroup w = g;
-            if (sub) {
-                w.tb = (int32_t)h.rows.size();
-                for (int k = g.tb; k < g.te; ++k) {
-                    const int t = pl->order[k];
-                    if (std::abs(pl->zt[t]) <= zs && std::abs(pl->wt[t]) <= ws) {
-                        h.rows.push_back(k);
-                        h.tl.push_back(t);
+        // a partial search: templates outside the range that make a row of a range fundamental
+        std::vector<char> extra;
+        if (range) {
+            extra.assign(pl->T, 0);
+            const int64_t *sl = h.slen.data() + (size_t)i * pl->n_entries;
+            for (int t = 0; t < pl->T; ++t)
+                if (t < t_lo || t >= t_hi)
+                    for (int e = pl->h_slot_beg[t]; e < pl->h_slot_beg[t + 1]; ++e)
+                        if (sl[e] > 0) extra[t] = 1;
+        }
+        for (int part = 0; part < (range ? 2 : 1); ++part) {
+            if (part == 1) L.stat_ctas = L.total_ctas - L.item_cta0[i];
+            for (const auto &g : pl->groups) {
+                ConvGroup w = g;
+                if (sub) {
+                    w.tb = (int32_t)h.rows.size();
+                    for (int k = g.tb; k < g.te; ++k) {
+                        const int t = pl->order[k];
+                        const bool in = range ? (part == 0 ? (t >= t_lo && t < t_hi) : extra[t] != 0)
+                                              : (std::abs(pl->zt[t]) <= zs && std::abs(pl->wt[t]) <= ws);
+                        if (in) {
+                            h.rows.push_back(k);
+                            h.tl.push_back(t);
+                        }
                     }
+                    w.te = (int32_t)h.rows.size();
+                    if (w.te == w.tb) continue;
                 }
-                w.te = (int32_t)h.rows.size();
-                if (w.te == w.tb) continue;
+                if (part == 0) nt_item += w.te - w.tb;
+                w.cta0 = (int32_t)L.total_ctas;
+                w.item = i;
+                h.work.push_back(w);
+                L.total_ctas += ((bN + g.V - 1) / g.V + segs - 1) / segs;
             }
-            nt_item += w.te - w.tb;
-            w.cta0 = (int32_t)L.total_ctas;
-            w.item = i;
-            h.work.push_back(w);
-            L.total_ctas += ((bN + g.V - 1) / g.V + segs - 1) / segs;
         }
         L.item_cta0[i + 1] = L.total_ctas;
         L.harm0[i + 1] = L.harm0[i] + harm_blocks_for(pl, n[i]);
@@ -393,6 +422,7 @@ jerk_status plan_tables(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64
         for (int si = 1; si < ns; ++si)
             h.counts[(size_t)i * JERK_MAX_STAGES + si] = (double)nf_stage[si] * n_cells(bN, pl->prm.stages[si]);
     }
+    L.counts_host = h.counts;
     ConvGroup end;
     std::memset(&end, 0, sizeof(end));
     end.cta0 = (int32_t)L.total_ctas;
@@ -422,9 +452,10 @@ void fill_items(const jerk_plan_s *pl, const BatchLayout &L, HostTables &h) {
 
 // Cached tables: own device buffers, synchronous upload.
 jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int64_t> &n,
-                         const std::vector<int32_t> &zm, const std::vector<int32_t> &wm) {
+                         const std::vector<int32_t> &zm, const std::vector<int32_t> &wm, int32_t t_lo = 0,
+                         int32_t t_hi = -1) {
     HostTables h;
-    const jerk_status s = plan_tables(pl, L, n, zm, wm, h);
+    const jerk_status s = plan_tables(pl, L, n, zm, wm, h, t_lo, t_hi);
     if (s != JERK_OK) return s;
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMalloc(&L.d_items, sizeof(ItemDesc) * h.items.size());
@@ -454,9 +485,9 @@ jerk_status build_layout(jerk_plan_s *pl, BatchLayout &L, const std::vector<int6
 // Launch tables for a set of spectrum lengths (and sub-grids): reused from a
 // small LRU cache, built on first use (a host synchronisation).
 jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, const std::vector<int32_t> &zm,
-                          const std::vector<int32_t> &wm, cudaStream_t st) {
+                          const std::vector<int32_t> &wm, cudaStream_t st, int32_t t_lo = 0, int32_t t_hi = -1) {
     for (BatchLayout *L : pl->layouts)
-        if (L->n == n && L->zmax == zm && L->wmax == wm) {
+        if (L->n == n && L->zmax == zm && L->wmax == wm && L->t_lo == t_lo && L->t_hi == t_hi) {
             L->last_use = ++pl->use_clock;
             pl->cur = L;
             return JERK_OK;
@@ -473,7 +504,7 @@ jerk_status ensure_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, const 
         if (!L) return JERK_ENOMEM;
         pl->layouts.push_back(L);
     }
-    const jerk_status s = build_layout(pl, *L, n, zm, wm);
+    const jerk_status s = build_layout(pl, *L, n, zm, wm, t_lo, t_hi);
     if (s != JERK_OK) {
         free_layout(*L);
         pl->layouts.erase(std::find(pl->layouts.begin(), pl->layouts.end(), L));
@@ -566,7 +597,10 @@ jerk_status transient_layout(jerk_plan_s *pl, const std::vector<int64_t> &n, con
 // Enqueue the whole path for the spectra of the current layout.  in[i] is
 // spectrum i (device).  Capturable into a CUDA graph (no host copies, no
 // host synchronisation, no event waits).
-jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_t st, bool capturing) {
+jerk_status enqueue_peaks(jerk_plan_s *pl, cudaStream_t st);
+
+jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_t st, bool capturing,
+                           bool peaks = true) {
     const BatchLayout &L = *pl->cur;
     const int count = (int)L.n.size();
     const int ns = pl->prm.n_stages;
@@ -637,7 +671,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
     }
     JCHECK(mark(pl, 3, st, capturing));
     for (int i = 0; i < count; ++i)
-        JCHECK(launch_finalise_stats(pl->d_stat_part + 2 * L.item_cta0[i], L.item_cta0[i + 1] - L.item_cta0[i],
+        JCHECK(launch_finalise_stats(pl->d_stat_part + 2 * L.item_cta0[i],
+                                     L.stat_ctas >= 0 ? L.stat_ctas : L.item_cta0[i + 1] - L.item_cta0[i],
                                      partH + 2 * ns * L.harm0[i], L.harm0[i + 1] - L.harm0[i], ns,
                                      L.d_counts + (size_t)i * JERK_MAX_STAGES, pl->d_thresh, pl->prm.thresh_mode,
                                      pl->d_stats + (size_t)i * 2 * JERK_MAX_STAGES,
@@ -645,6 +680,19 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
 
     // peaks
     JCHECK(mark(pl, 4, st, capturing));
+    if (peaks) {
+        const jerk_status ps = enqueue_peaks(pl, st);
+        if (ps != JERK_OK) return ps;
+    }
+    JCHECK(mark(pl, 5, st, capturing));
+    return JERK_OK;
+}
+
+// thresholded peaks of every spectrum of the current layout (Sec. 3)
+jerk_status enqueue_peaks(jerk_plan_s *pl, cudaStream_t st) {
+    const BatchLayout &L = *pl->cur;
+    const int count = (int)L.n.size();
+    const int ns = pl->prm.n_stages;
     JCHECK(cudaMemsetAsync(pl->d_count, 0, sizeof(unsigned long long), st));
     for (int i = 0; i < count; ++i) {
         const int64_t bN = (int64_t)pl->b * L.n[i];
@@ -660,9 +708,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
         pk.out = pl->d_cand;
         pk.cap = pl->prm.max_candidates;
         pk.count = pl->d_count;
-        JCHECK(launch_peaks(pk, st));
+        JCHECK(launch_peaks(pk, pl->sms, st));
     }
-    JCHECK(mark(pl, 5, st, capturing));
     return JERK_OK;
 }
 
@@ -682,6 +729,7 @@ jerk_status finish_search(jerk_plan_s *pl, cudaStream_t st, int count, bool prof
     pl->last_count = count;
     pl->searched = true;
     pl->profiled = profiled;
+    pl->partial = false;
     return JERK_OK;
 }
 
@@ -786,7 +834,9 @@ jerk_status plan_memory(jerk_plan_s *pl, bool own_bank) {
                    (int64_t)pl->max_batch * 32 * std::max(1, pl->n_fund * JERK_MAX_HARMONIC);
     const int64_t conv_blocks = ctas_for(pl, N) + (int64_t)pl->max_batch * (int64_t)pl->groups.size();
     const int64_t harm_blocks = harm_blocks_for(pl, N) + pl->max_batch;
-    pl->stat_part_cap = 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
+    // (a partial search by template range runs each group's templates of the range
+    // and, separately, the other templates its fundamentals need: up to twice the CTAs)
+    pl->stat_part_cap = 2 * 2 * conv_blocks + 2 * (int64_t)ns * harm_blocks;
 
     // does it fit?
     size_t free_b = 0, total_b = 0;
@@ -886,6 +936,8 @@ const char *jerk_status_str(jerk_status s) {
     return "unknown jerk_status";
 }
 
+jerk_status jerk_params_validate(const jerk_params *params) { return validate(params); }
+
 jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *out) {
     if (!out) return JERK_EINVAL;
     *out = nullptr;
@@ -899,6 +951,7 @@ jerk_status jerk_plan_create(const jerk_params *params, int device, jerk_plan *o
     if (!pl) return JERK_ENOMEM;
     pl->prm = *params;
     pl->device = device;
+    pl->sms = device_sms(device);
     pl->max_batch = std::max(1, params->max_batch);
     v = plan_structure(pl);
     if (v == JERK_OK) v = plan_memory(pl, true);
@@ -932,6 +985,7 @@ jerk_status jerk_plan_share(jerk_plan parent, const jerk_params *params, jerk_pl
     pl->prm = *params;
     pl->prm.seg_len = parent->L;
     pl->device = parent->device;
+    pl->sms = parent->sms;
     pl->max_batch = std::max(1, params->max_batch);
     // the parent's structure: its groups fix the tap offset baked into every bank row
     pl->b = parent->b;
@@ -1051,9 +1105,10 @@ jerk_status jerk_templates(jerk_plan pl, void *stream) {
                         pl->d_gl, pl->n_gl, taps, st);
         if (e == cudaSuccess)
             e = launch_template_fft(taps, d_shift + k0, d_klen + k0, nt, pl->K, pl->L, tw,
+                                    pl->prm.precision ? 0 : conv_fold_radix(pl->log2L),
                                     pl->d_bank + (size_t)k0 * pl->L, st);
     }
-    if (e == cudaSuccess) e = launch_bank_maxabs(pl->d_bank, (int64_t)pl->T * pl->L, pl->d_cmax, st);
+    if (e == cudaSuccess) e = launch_bank_maxabs(pl->d_bank, (int64_t)pl->T * pl->L, pl->d_cmax, pl->sms, st);
     cudaFreeAsync(taps, st);
     if (tw) cudaFreeAsync(tw, st);
     if (d_shift) cudaFreeAsync(d_shift, st);
@@ -1125,6 +1180,81 @@ jerk_status jerk_search(jerk_plan pl, const void *d_spec, int64_t n, void *strea
     s = enqueue_search(pl, in, st, false);
     if (s != JERK_OK) return s;
     return finish_search(pl, st, 1, pl->profile);
+}
+
+jerk_status jerk_search_range(jerk_plan pl, const void *d_spec, int64_t n, int32_t t_lo, int32_t t_hi,
+                              void *stream) {
+    if (!pl || !d_spec || n < 1 || n > pl->prm.max_bins) return JERK_EINVAL;
+    if (t_lo < 0 || t_hi > pl->T || t_lo >= t_hi) return JERK_EINVAL;
+    if (!bank_ready(pl)) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    static const std::vector<int32_t> none;
+    jerk_status s = ensure_layout(pl, std::vector<int64_t>{n}, none, none, st, t_lo, t_hi);
+    if (s != JERK_OK) return s;
+    const float2 *in[1] = {(const float2 *)d_spec};
+    s = enqueue_search(pl, in, st, false, false);
+    if (s != JERK_OK) return s;
+    JCHECK(cudaMemsetAsync(pl->d_count, 0, sizeof(unsigned long long), st));   // no candidates yet
+    s = finish_search(pl, st, 1, false);
+    pl->partial = true;
+    return s;
+}
+
+jerk_status jerk_range_sums(jerk_plan pl, double *h_sum, double *h_sumsq, double *h_count) {
+    if (!pl) return JERK_EINVAL;
+    if (!pl->searched || !pl->partial || !pl->cur) return JERK_ESTATE;
+    JCHECK(cudaSetDevice(pl->device));
+    JCHECK(cudaEventSynchronize(pl->done));
+    const jerk_status de = device_error(pl);
+    if (de != JERK_OK) return de;
+    const int ns = pl->prm.n_stages;
+    double st[2 * JERK_MAX_STAGES];
+    JCHECK(cudaMemcpy(st, pl->d_stats, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost));
+    for (int si = 0; si < ns; ++si) {
+        // the sums behind (mu, sd) = (S1 / n, sqrt(S2 / n - mu^2)) as computed on the device
+        const double cnt = pl->cur->counts_host[si], mu = st[2 * si], sd = st[2 * si + 1];
+        if (h_sum) h_sum[si] = mu * cnt;
+        if (h_sumsq) h_sumsq[si] = (sd * sd + mu * mu) * cnt;
+        if (h_count) h_count[si] = cnt;
+    }
+    return JERK_OK;
+}
+
+jerk_status jerk_select(jerk_plan pl, const double *h_sum, const double *h_sumsq, const double *h_count,
+                        void *stream) {
+    if (!pl) return JERK_EINVAL;
+    if (!pl->searched || !pl->cur || pl->cur->n.size() != 1) return JERK_ESTATE;
+    const bool sigma = pl->prm.thresh_mode == JERK_THRESH_SIGMA;
+    if (sigma && (!h_sum || !h_sumsq || !h_count)) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(pl->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int ns = pl->prm.n_stages;
+    double stats[2 * JERK_MAX_STAGES] = {0};
+    float theta[JERK_MAX_STAGES];
+    for (int si = 0; si < ns; ++si) {
+        // the same arithmetic as the device's finalisation of the statistics
+        double mu = 0.0, sd = 0.0;
+        theta[si] = pl->prm.thresh[si];
+        if (sigma && h_count[si] > 0.0) {
+            mu = h_sum[si] / h_count[si];
+            const double var = h_sumsq[si] / h_count[si] - mu * mu;
+            sd = std::sqrt(var > 0.0 ? var : 0.0);
+            theta[si] = (float)(mu + (double)pl->prm.thresh[si] * sd);
+        }
+        stats[2 * si] = mu;
+        stats[2 * si + 1] = sd;
+    }
+    JCHECK(cudaStreamWaitEvent(st, pl->done, 0));
+    JCHECK(cudaMemcpyAsync(pl->d_stats, stats, sizeof(double) * 2 * ns, cudaMemcpyHostToDevice, st));
+    JCHECK(cudaMemcpyAsync(pl->d_theta, theta, sizeof(float) * ns, cudaMemcpyHostToDevice, st));
+    const jerk_status s = enqueue_peaks(pl, st);
+    if (s != JERK_OK) return s;
+    JCHECK(cudaStreamSynchronize(st));             // the host arrays above are on the stack
+    JCHECK(cudaEventRecord(pl->done, st));
+    pl->partial = false;
+    return JERK_OK;
 }
 
 jerk_status jerk_search_batch_grid(jerk_plan pl, const void *const *d_specs, const int64_t *n, const int32_t *zmax,
@@ -1218,7 +1348,7 @@ jerk_status jerk_search_host(jerk_plan pl, const void *h_spec, int64_t n, void *
 
 jerk_status jerk_candidates(jerk_plan pl, jerk_candidate *h_out, int64_t cap, int64_t *n_out) {
     if (!pl || !n_out || cap < 0 || (cap > 0 && !h_out)) return JERK_EINVAL;
-    if (!pl->searched) return JERK_ESTATE;
+    if (!pl->searched || pl->partial) return JERK_ESTATE;
     JCHECK(cudaSetDevice(pl->device));
     JCHECK(cudaEventSynchronize(pl->done));
     {

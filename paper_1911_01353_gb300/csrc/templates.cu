@@ -16,7 +16,8 @@
 // panel starts a_j, c_{j,i} = W_i (h/2) exp(2 pi i (z u^2/2 + w u^3/6)).
 //
 // The length-L spectrum of each tap vector is then taken by an FP64
-// radix-2 FFT in shared memory and stored as FP32 with 1/L folded in.
+// radix-2 FFT in shared memory and stored as FP32 with 1/L folded in (for
+// the FP32 filter in the folded form described at template_fft_kernel).
 #include <cmath>
 #include <vector>
 
@@ -137,9 +138,18 @@ __global__ void twiddle64_kernel(double2 *tw, int L) {
 // G[f] = (1/L) sum_{m<Kg} g[m] exp(+2 pi i f m / L): radix-2 DIT in shared
 // memory.  Row i holds taps at index d + bM (bank-wide offset); the template's
 // group uses offset bM - shift[i], i.e. g[m] = taps[i][m + shift[i]], m < klen[i].
+//
+// fold_r0 > 0 stores the row in the folded form the FP32 filter multiplies
+// with (its inverse transform's first pass has radix R0 = fold_r0 over the
+// elements f = j + (L/16)(i + (16/R0) k)): the spread segment has zeros at
+// every odd cell, so its spectrum X has period L/2, and that pass splits
+// into two DFTs of R0/2 points on
+//   f < L/2:   G[f] + G[f + L/2],
+//   f >= L/2:  (G[f - L/2] - G[f]) exp(+2 pi i k / R0),  k = ((f - L/2) / (L/16)) / (16 / R0),
+// both computed in FP64 before the one rounding to FP32.
 __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int32_t *__restrict__ shift,
                                     const int32_t *__restrict__ klen, int K, int L, int log2L,
-                                    const double2 *__restrict__ tw, float2 *__restrict__ bank) {
+                                    const double2 *__restrict__ tw, int fold_r0, float2 *__restrict__ bank) {
     extern __shared__ double2 buf[];   // [L]
     const double2 *g = taps + (int64_t)blockIdx.x * K;
     const int sh = shift[blockIdx.x], kl = klen[blockIdx.x];
@@ -164,6 +174,23 @@ __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int3
     }
     float2 *dst = bank + (int64_t)blockIdx.x * L;
     const double inv = 1.0 / L;
+    if (fold_r0 > 0) {
+        const int half = L / 2, nt = L / 16, i0 = 16 / fold_r0;
+        for (int f = threadIdx.x; f < L; f += blockDim.x) {
+            double2 v;
+            if (f < half) {
+                v = make_double2(buf[f].x + buf[f + half].x, buf[f].y + buf[f + half].y);
+            } else {
+                const double2 d = make_double2(buf[f - half].x - buf[f].x, buf[f - half].y - buf[f].y);
+                const int k = ((f - half) / nt) / i0;
+                double sw, cw;
+                sincospi(2.0 * k / fold_r0, &sw, &cw);
+                v = make_double2(d.x * cw - d.y * sw, d.x * sw + d.y * cw);
+            }
+            dst[f] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+        }
+        return;
+    }
     for (int f = threadIdx.x; f < L; f += blockDim.x)
         dst[f] = make_float2((float)(buf[f].x * inv), (float)(buf[f].y * inv));
 }
@@ -180,10 +207,10 @@ __global__ void bank_maxabs_kernel(const float2 *__restrict__ bank, int64_t n, i
     if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_int(m));
 }
 
-cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, cudaStream_t st) {
+cudaError_t launch_bank_maxabs(const float2 *bank, int64_t n, float *out, int sms, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float), st);
     if (e != cudaSuccess) return e;
-    bank_maxabs_kernel<<<152 * 4, 256, 0, st>>>(bank, n, reinterpret_cast<int *>(out));
+    bank_maxabs_kernel<<<sms * 4, 256, 0, st>>>(bank, n, reinterpret_cast<int *>(out));
     return cudaGetLastError();
 }
 
@@ -206,14 +233,14 @@ cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st) {
 }
 
 cudaError_t launch_template_fft(const double2 *taps, const int32_t *shift, const int32_t *klen, int32_t nt, int K,
-                                int L, const double2 *tw, float2 *bank, cudaStream_t st) {
+                                int L, const double2 *tw, int fold_r0, float2 *bank, cudaStream_t st) {
     int log2L = 0;
     while ((1 << log2L) < L) ++log2L;
     const size_t sm = (size_t)L * sizeof(double2);
     cudaError_t e =
         cudaFuncSetAttribute(template_fft_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    template_fft_kernel<<<nt, 512, sm, st>>>(taps, shift, klen, K, L, log2L, tw, bank);
+    template_fft_kernel<<<nt, 512, sm, st>>>(taps, shift, klen, K, L, log2L, tw, fold_r0, bank);
     return cudaGetLastError();
 }
 

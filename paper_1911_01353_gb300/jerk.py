@@ -8,6 +8,7 @@ library is missing the import of ``lib()`` raises: there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 import numpy as np
@@ -26,7 +27,8 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
            "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits",
-           "jerk_measure_peaks", "jerk_check_counts")
+           "jerk_measure_peaks", "jerk_check_counts", "jerk_params_validate", "jerk_search_range",
+           "jerk_range_sums", "jerk_select", "jerk_subharmonic")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -82,6 +84,13 @@ def lib() -> ctypes.CDLL:
         st = ctypes.c_int
         sig = {
             "jerk_plan_create": ([ctypes.POINTER(Params), ctypes.c_int, ctypes.POINTER(vp)], st),
+            "jerk_params_validate": ([ctypes.POINTER(Params)], st),
+            "jerk_search_range": ([vp, vp, i64, i32, i32, vp], st),
+            "jerk_subharmonic": ([vp, vp, i64, i32, vp, vp, vp], st),
+            "jerk_range_sums": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double)], st),
+            "jerk_select": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), vp], st),
             "jerk_templates": ([vp, vp], st),
             "jerk_search": ([vp, vp, i64, vp], st),
             "jerk_search_host": ([vp, vp, i64, vp], st),
@@ -229,6 +238,75 @@ class Plan:
         _check(lib().jerk_search(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(),
                                  _stream_handle(stream)), "jerk_search")
 
+    def search_range(self, spec, t_lo: int, t_hi: int, stream=None):
+        """Enqueue a partial search over templates t_lo <= t < t_hi
+        (jerk_search_range); merge with the other ranges, then select()."""
+        assert spec.is_cuda and spec.is_contiguous() and str(spec.dtype) == "torch.complex64"
+        _check(lib().jerk_search_range(self._h, ctypes.c_void_p(spec.data_ptr()), spec.numel(), int(t_lo),
+                                       int(t_hi), _stream_handle(stream)), "jerk_search_range")
+
+    def range_sums(self):
+        """(sum, sum of squares, count) per stage of the last partial search
+        (jerk_range_sums); synchronises."""
+        ns = int(self.params.n_stages)
+        a, b, c = (ctypes.c_double * ns)(), (ctypes.c_double * ns)(), (ctypes.c_double * ns)()
+        _check(lib().jerk_range_sums(self._h, a, b, c), "jerk_range_sums")
+        return np.array(a[:]), np.array(b[:]), np.array(c[:])
+
+    def select(self, sums=None, sumsq=None, counts=None, stream=None):
+        """Thresholds from (reduced) sums and the peaks of the current
+        max-projections (jerk_select); synchronises."""
+        ns = int(self.params.n_stages)
+
+        def arr(x):
+            return None if x is None else (ctypes.c_double * ns)(*[float(v) for v in x])
+        _check(lib().jerk_select(self._h, arr(sums), arr(sumsq), arr(counts), _stream_handle(stream)),
+               "jerk_select")
+
+    def search_subharmonic(self, spec, cap: int = 1 << 16, stream=None):
+        """The search with the harmonic sum indexed by the highest harmonic
+        (jerk_subharmonic) for every stage of the plan: the whole power plane
+        (jerk_plane, n_templates x b n floats, allocated here), per stage the
+        max-projection and sums of S'_H, the threshold (the plan's mode and
+        values) and the peaks (jerk_peaks_noalloc).  Synchronises.  Returns
+        (candidate records, [(mu, sd, theta)] per stage, [packed int64
+        max-projection tensors])."""
+        import torch
+        n = spec.numel()
+        T, bN = int(self.info.n_templates), 2 * n
+        dev = torch.device("cuda", self.device)
+        plane = torch.empty((T, bN), dtype=torch.float32, device=dev)
+        self.plane(spec, 0, T, plane, stream=stream)
+        p = self.params
+        recs, stats, maxprojs = [], [], []
+        for si in range(int(p.n_stages)):
+            H = int(p.stages[si])
+            M = torch.empty(bN, dtype=torch.int64, device=dev)
+            sums = torch.zeros(2, dtype=torch.float64, device=dev)
+            _check(lib().jerk_subharmonic(self._h, ctypes.c_void_p(plane.data_ptr()), n, H,
+                                          ctypes.c_void_p(M.data_ptr()), ctypes.c_void_p(sums.data_ptr()),
+                                          _stream_handle(stream)), "jerk_subharmonic")
+            torch.cuda.synchronize(self.device)
+            s1, s2 = (float(x) for x in sums.cpu())
+            cnt = float(T) * float(bN)
+            mu = s1 / cnt
+            sd = math.sqrt(max(0.0, s2 / cnt - mu * mu))
+            theta = float(np.float32(mu + float(p.thresh[si]) * sd)) if p.thresh_mode == THRESH_SIGMA \
+                else float(np.float32(p.thresh[si]))
+            out = torch.zeros(cap * CANDIDATE_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+            cnt_d = torch.zeros(1, dtype=torch.int64, device=dev)
+            peaks_noalloc(M.data_ptr(), bN, theta, H, int(p.zmax), int(p.dz), int(p.wmax), int(p.dw),
+                          out.data_ptr(), cap, cnt_d.data_ptr(), stream)
+            torch.cuda.synchronize(self.device)
+            k = int(cnt_d.item())
+            if k > cap:
+                raise JerkError(JERK_EOVERFLOW, "jerk_peaks_noalloc (%d found)" % k)
+            raw = out[: k * CANDIDATE_DTYPE.itemsize].cpu().numpy()
+            recs.extend(np.frombuffer(raw.tobytes(), dtype=CANDIDATE_DTYPE).tolist())
+            stats.append((mu, sd, theta))
+            maxprojs.append(M)
+        return recs, stats, maxprojs
+
     def share(self, params: Params) -> "Plan":
         """A new plan over this plan's template bank with its own workspace
         (jerk_plan_share)."""
@@ -372,6 +450,14 @@ class Plan:
         _check(lib().jerk_maxproj(self._h, item, stage_idx, ctypes.byref(ptr), ctypes.byref(n)), "jerk_maxproj")
         return ptr.value, n.value
 
+    def maxproj_tensor(self, stage_idx: int, item: int = 0):
+        """The packed stage max-projection in place on the device, as an int64
+        CUDA tensor view (writable; valid until the plan's next search).  The
+        packed entries are non-negative, so signed and unsigned order agree."""
+        import torch
+        ptr, n = self.maxproj_ptr(stage_idx, item)
+        return torch.as_tensor(_DevArray(ptr, n, "<i8"), device="cuda:%d" % self.device)
+
     def maxproj(self, stage_idx: int, item: int = 0):
         """Copy the packed stage max-projection to host: (float32 M, int64 t)."""
         import torch
@@ -385,7 +471,7 @@ class Plan:
 
 
 class _DevArray:
-    """A read-only view of library-owned device memory for torch.as_tensor."""
+    """A view of library-owned device memory for torch.as_tensor."""
 
     def __init__(self, ptr: int, n: int, typestr: str):
         self.__cuda_array_interface__ = {"shape": (n,), "typestr": typestr,

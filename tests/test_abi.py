@@ -55,17 +55,43 @@ def test_status_strings(L):
     assert b"unknown" in L.jerk_status_str(99)
 
 
-@pytest.mark.parametrize("field,value", [("dz", 0), ("zmax", 21), ("numbetween", 4), ("pad_bins", 0),
-                                         ("seg_len", 3000), ("n_stages", 0), ("norm_block", 5000),
-                                         ("precision", 1), ("max_bins", 0), ("max_candidates", 0),
-                                         ("thresh_mode", 7)])
+INVALID = [("dz", 0), ("zmax", 21), ("numbetween", 4), ("pad_bins", 0), ("seg_len", 3000),
+           ("seg_len", 16384), ("n_stages", 0), ("n_stages", 5), ("norm_block", 5000), ("precision", 3),
+           ("precision", -1), ("max_bins", 0), ("max_bins", (1 << 29) + 1), ("max_candidates", 0),
+           ("max_batch", -1), ("thresh_mode", 7), ("zmax", 4098), ("wmax", 32780)]
+
+
+def test_valid_params_accepted_without_gpu(L):
+    """The validation itself (no device involved) accepts the parameter sets
+    the tests and the benchmark use, including the reduced-precision filters."""
+    from paper_1911_01353_gb300 import jerk
+    for kw in (dict(), dict(precision=1), dict(precision=2, seg_len=4096), dict(seg_len=8192),
+               dict(stages=(1, 2, 4, 8), thresh=(1, 1, 1, 1)), dict(stages=(1, 3), thresh=(1, 1))):
+        p = jerk.make_params(20, 2, 60, 20, **kw)
+        assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_OK, kw
+    p = jerk.make_params(200, 2, 600, 20, stages=(1, 2, 4, 8), thresh=(19, 17, 15, 14),
+                         thresh_mode=jerk.THRESH_SIGMA, max_bins=1 << 22)
+    assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_OK
+
+
+@pytest.mark.parametrize("field,value", INVALID)
 def test_invalid_params_rejected_without_gpu(L, field, value):
+    """Each invalid field is rejected by the validation alone (no device), and
+    jerk_plan_create then fails and leaves the handle NULL."""
     from paper_1911_01353_gb300 import jerk
     p = jerk.make_params(20, 2, 60, 20)
+    assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_OK
     setattr(p, field, value)
+    assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_EINVAL
     h = ctypes.c_void_p(123)
     assert L.jerk_plan_create(ctypes.byref(p), 0, ctypes.byref(h)) == jerk.JERK_EINVAL
     assert h.value is None
+
+
+def test_tensor_core_filter_needs_its_segment_length(L):
+    from paper_1911_01353_gb300 import jerk
+    p = jerk.make_params(20, 2, 60, 20, precision=2, seg_len=2048)
+    assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_EINVAL
 
 
 def test_bad_stage_lists_rejected(L):
@@ -73,6 +99,7 @@ def test_bad_stage_lists_rejected(L):
     for stages in ((2,), (1, 1), (1, 4, 2), (1, 16)):
         p = jerk.make_params(20, 2, 60, 20, stages=stages, thresh=(1, 1, 1, 1))
         h = ctypes.c_void_p()
+        assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_EINVAL
         assert L.jerk_plan_create(ctypes.byref(p), 0, ctypes.byref(h)) == jerk.JERK_EINVAL
 
 
@@ -83,3 +110,4 @@ def test_null_handles(L):
     n = ctypes.c_int64()
     assert L.jerk_candidates(None, None, 0, ctypes.byref(n)) == jerk.JERK_EINVAL
     assert L.jerk_plan_create(None, 0, None) == jerk.JERK_EINVAL
+    assert L.jerk_params_validate(None) == jerk.JERK_EINVAL

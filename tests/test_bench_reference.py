@@ -1,4 +1,4 @@
-"""The reference arm of bench.py (the FP64 CPU oracle on a bounded sample of
+"""The reference arm of bench.py (the FP64 CPU oracle's FFT route on a bounded sample of
 the workload) prints one JSON line with the fields the benchmark contract
 names; it needs no GPU."""
 import json
@@ -23,7 +23,7 @@ def test_reference_arm_line():
                 "higher_is_better", "dtype", "config", "cpu_baseline", "e2e"):
         assert key in line, key
     assert line["value"] > 0 and line["higher_is_better"] is True
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["cpu_baseline"]["kind"] == "oracle FFT route" and line["cpu_baseline"]["cores"] >= 1
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0

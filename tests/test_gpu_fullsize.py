@@ -14,7 +14,11 @@ by one (direct correlation in FP64) and properties that hold at any size:
   candidates satisfy the peak rule on the GPU's own max-projection;
 * the injected signals show in the max-projection at their frequencies;
 * the statistics are those of unit noise (mean = tap energy, sigma = mean)
-  and grow as H and sqrt(H) over the stages.
+  and grow as H and sqrt(H) over the stages;
+* against the oracle's whole-bank result by its FFT route (stored under
+  tests/golden/ by make_paper_scale.py): the candidate list of every stage
+  exactly (outside a guard band around FP32 decisions), mu_H and sigma_H, and
+  M_H with its argmax at 2^16 sampled cells per stage.
 
 Tolerance: PLANE_TOL of the plane maximum per power, H times that for a sum
 of H powers; the reduced-precision filters with their own bounds.
@@ -159,6 +163,102 @@ def test_full_size_statistics(full):
         assert theta[si] == pytest.approx(mu[si] + T_SIGMA[si] * sd[si], rel=1e-5)
 
 
+def _golden():
+    """The FP64 oracle's result for this workload by its FFT route, written by
+    tests/golden/make_paper_scale.py (which calls only oracle/ and synth/)."""
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    with open(os.path.join(here, "paper_scale_candidates.json")) as f:
+        g = json.load(f)
+    return g, np.load(os.path.join(here, "paper_scale_maxproj_sample.npz"))
+
+
+def test_golden_matches_this_workload(full):
+    g, _ = _golden()
+    q, op = g["params"], full["op"]
+    assert g["workload"] == full["wl"].name
+    assert (q["zmax"], q["dz"], q["wmax"], q["dw"], tuple(q["stages"]), q["thresh_mode"], tuple(q["thresh"]),
+            q["norm_block"], q["pad_bins"]) == (op.zmax, op.dz, op.wmax, op.dw, tuple(op.stages), op.thresh_mode,
+                                                tuple(op.thresh), op.norm_block, op.pad_bins)
+
+
+def test_full_size_statistics_equal_oracle(full):
+    """mu_H and sigma_H of every stage against the oracle's FP64 values over
+    all 1.03e11 stage-1 cells (and every defined cell of S_2, S_4, S_8)."""
+    g, _ = _golden()
+    mu, sd, theta = full["stats"]
+    for si, H in enumerate(full["op"].stages):
+        st = g["stages"][str(H)]
+        assert mu[si] == pytest.approx(st["mu"], rel=1e-5), H
+        assert sd[si] == pytest.approx(st["sigma"], rel=1e-5), H
+        assert theta[si] == pytest.approx(st["theta"], rel=1e-5), H
+
+
+def test_full_size_candidates_equal_oracle_list(full):
+    """The GPU's candidate list against the oracle's, exactly: every oracle
+    candidate is found with the same template and its power within H x the
+    tolerance, and every GPU candidate is an oracle candidate.  A cell is
+    guarded (left out) only when one of its decisions -- above theta, above
+    the left neighbour, not below the right one -- is within 2 H x the
+    tolerance of flipping in the oracle (theta widened by the GPU's own
+    difference from the oracle's theta); the template is compared wherever the
+    oracle's best and runner-up differ by more than that."""
+    g, _ = _golden()
+    tol = PLANE_TOL * g["plane_max"]
+    mu, sd, theta = full["stats"]
+    got = {(int(c.stage), int(c.p)): (int(c.t), float(c.power)) for c in full["cands"]}
+    total = guarded = 0
+    for si, H in enumerate(full["op"].stages):
+        st = g["stages"][str(H)]
+        band = 2 * H * tol
+        dth = abs(float(theta[si]) - st["theta"])
+        want = {r[0]: r for r in st["candidates"]}
+        near = {r[0]: r for r in st["near"]}
+
+        def is_guarded(r):
+            p, t, m, sec, left, right = r
+            left = -np.inf if left is None else left
+            right = -np.inf if right is None else right
+            return abs(m - st["theta"]) <= band + dth or abs(m - left) <= band or abs(m - right) <= band
+
+        for p, r in want.items():
+            total += 1
+            if is_guarded(r):
+                guarded += 1
+                continue
+            assert (H, p) in got, "oracle candidate (H=%d, p=%d, M=%g) missing on the GPU" % (H, p, r[2])
+            t, power = got[(H, p)]
+            assert abs(power - r[2]) <= H * tol, (H, p, power, r[2])
+            if r[2] - r[3] > band:
+                assert t == r[1], "template differs at (H=%d, p=%d): %d vs %d" % (H, p, t, r[1])
+        for (h, p) in got:
+            if h != H or p in want:
+                continue
+            assert p in near and is_guarded(near[p]), "GPU candidate (H=%d, p=%d) is not an oracle candidate" % (H, p)
+            guarded += 1
+    assert total > 100
+    assert guarded <= max(4, total // 50), (guarded, total)
+
+
+def test_full_size_maxproj_equals_oracle_sample(full):
+    """M_H and its argmax at the stored cells (65 536 random cells per stage
+    plus +-4 around every candidate) against the oracle's FFT-route values."""
+    g, z = _golden()
+    tol = PLANE_TOL * g["plane_max"]
+    for si, H in enumerate(full["op"].stages):
+        ps = z["p%d" % H].astype(np.int64)
+        m, t, sec = z["m%d" % H].astype(np.float64), z["t%d" % H], z["s%d" % H].astype(np.float64)
+        Mv, Mt = full["M"][si]
+        assert Mv.size == g["stages"][str(H)]["cells"]
+        err = np.abs(Mv[ps].astype(np.float64) - m)
+        assert err.max() <= H * tol, (H, float(err.max()))
+        sure = m - sec > 2 * H * tol
+        assert sure.mean() > 0.5
+        bad = np.nonzero(sure & (Mt[ps] != t))[0]
+        assert bad.size == 0, (H, ps[bad[:5]], Mt[ps][bad[:5]], t[bad[:5]])
+
+
 @pytest.mark.parametrize("prec", [1, 2])
 def test_full_size_tensor_core_rows(full, pkg, prec):
     op, Fn, x = full["op"], full["Fn"], full["x"]
@@ -241,3 +341,17 @@ def test_served_size_subgrid_request(pkg):
     assert np.max(np.abs(bank.power_cells(Fn, t[cells], cells) - M[cells])) <= tol
     want = bank.power_cells(Fn, [int(c.t) for c in recs], [int(c.p) for c in recs])
     assert np.max(np.abs(want - np.array([c.power for c in recs]))) <= tol
+
+
+def test_full_size_split_by_template_range(full):
+    """The benchmark's search split in two template ranges (as two GPUs would
+    run it), merged: max-projections bitwise equal to the whole-bank search,
+    statistics to the order of FP64 additions, the same candidates.  Runs on
+    the fixture's plan, so it comes last in this file."""
+    from test_gpu_split import compare, split_search
+
+    from paper_1911_01353_gb300.ranks import template_range
+    plan, x = full["plan"], full["x"]
+    T = plan.info.n_templates
+    split_search(plan, x, [template_range(T, r, 2) for r in range(2)])
+    compare(plan, full["M"], full["cands"], full["stats"], True)

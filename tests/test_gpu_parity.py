@@ -104,12 +104,28 @@ def test_taps_paper_scale_sample(pkg):
             assert np.max(np.abs(got - want)) < 1e-11, (t, zt[t], wt[t])
 
 
-def test_bank_spectra(pkg):
+def fold_spectrum(G, L):
+    """The folded form the FP32 filter's bank stores (sums of the two halves of
+    G, then their differences times exp(+2 pi i k / R0), k the element's DFT
+    index in the first inverse pass of radix R0)."""
+    log2L = int(round(np.log2(L)))
+    R0 = 1 << (log2L % 4) if log2L % 4 else 16
+    NT, I0, h = L // 16, 16 // R0, L // 2
+    f = np.arange(h)
+    k = (f // NT) // I0
+    return np.concatenate([G[:h] + G[h:], (G[:h] - G[h:]) * np.exp(2j * np.pi * k / R0)])
+
+
+@pytest.mark.parametrize("precision,seg_len", [(0, 0), (0, 2048), (0, 8192), (2, 0)])
+def test_bank_spectra(pkg, precision, seg_len):
     """Stored FP32 template spectra = (1/L) sum_m g[m] e^{+2 pi i f m / L} of the
-    oracle's taps (NumPy FFT), to FP32 rounding."""
+    oracle's taps (NumPy FFT), to FP32 rounding: as such for the tensor-core
+    filters, in the folded form for the FP32 filter."""
     wl = synth.small_single()
     op = oracle_params(wl)
-    with pkg.Plan(jerk_params(op, 1 << 16)) as plan:
+    p = jerk_params(op, 1 << 16, seg_len=seg_len)
+    p.precision = precision
+    with pkg.Plan(p) as plan:
         L, K, T = plan.info.seg_len, plan.info.taps, plan.info.n_templates
         torch.cuda.synchronize()
         from paper_1911_01353_gb300.jerk import _DevArray
@@ -128,6 +144,8 @@ def test_bank_spectra(pkg):
         g = np.zeros(L, complex)
         g[bMg - D: bMg + D + 1] = c
         want = np.fft.ifft(g)          # (1/L) sum_m g[m] e^{+2 pi i f m / L}
+        if precision == 0:
+            want = fold_spectrum(want, L)
         assert np.max(np.abs(bank[row] - want)) < 2e-7 * np.max(np.abs(want)) + 1e-9
     assert len(rows) == 5
 

@@ -467,3 +467,66 @@ def test_power_cells_equal_correlate():
     got = bank.power_cells(Fn, tt, pp)
     want = np.array([full[int(t)][int(q)] for t, q in zip(tt, pp)])
     assert np.max(np.abs(got - want)) <= 1e-13 * max(1.0, want.max())
+
+
+# ---------------------------------------------------------------------------
+# The sub-harmonic form (harmonic sum indexed by the highest harmonic)
+# ---------------------------------------------------------------------------
+
+def test_round_ratio_by_hand():
+    a = np.array([-7, -5, -3, -1, 0, 1, 3, 5, 7])
+    assert oracle.round_ratio(a, 1, 2).tolist() == [-4, -3, -2, -1, 0, 1, 2, 3, 4]     # halves away from 0
+    assert oracle.round_ratio([10, 11, 12], 1, 3).tolist() == [3, 4, 4]
+    assert oracle.round_ratio([10, 11, 12], 2, 3).tolist() == [7, 7, 8]
+    assert oracle.round_ratio([9], 5, 8).tolist() == [6]                                # 5.625 -> 6
+    assert oracle.round_ratio([-9], 3, 8).tolist() == [-3]                              # -3.375 -> -3
+
+
+def test_subharmonic_templates_by_hand():
+    p = oracle.Params(20, 2, 60, 20)                       # z index -10..10, w index -3..3
+    sub = oracle.subharmonic_templates(p, 4)
+    t = 6 * 21 + 17                                        # w = +60 (j = 6), z = +14 (i = 17)
+    want = []
+    for zi, wi in ((2, 1), (4, 2), (5, 2), (7, 3)):         # round(h 7 / 4), round(h 3 / 4), h = 1..4
+        want.append((wi + 3) * 21 + zi + 10)
+    assert sub[t].tolist() == want
+    assert np.array_equal(oracle.subharmonic_templates(p, 1)[:, 0], np.arange(p.n_templates))
+
+
+@pytest.mark.parametrize("H", [2, 3, 4])
+def test_subharmonic_sum_equals_fundamental_sum_where_exact(H):
+    """Where the top harmonic sits at (H q, H z, H w) every rounding is exact,
+    and the sub-harmonic sum adds the very terms of the fundamental-indexed
+    sum S_H(q, z, w), in the same order: the two are bitwise equal there."""
+    wl = synth.Workload("t", 3000, 20, 2, 60, 20, (1, H), (10.0, 10.0), 7,
+                        [synth.Signal(300.5, 4.0, 20.0, 40.0, 0.2)], harmonics=H)
+    p = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=(1, H))
+    Fn = oracle.normalise(wl.make(), p.norm_block)
+    P = oracle.plane(Fn, p)
+    Sp = oracle.subharmonic_sums(P, p, H)
+    fund, S = oracle.harmonic_sums(P, p)[H]
+    zt, wt = oracle.grid(p)
+    for k, f in enumerate(fund):
+        top = ((H * wt[f] + p.wmax) // p.dw) * p.nz + (H * zt[f] + p.zmax) // p.dz
+        q = np.arange(S.shape[1])
+        assert np.array_equal(Sp[top, H * q], S[k])
+
+
+def test_subharmonic_search_finds_the_top_harmonic():
+    """A signal with 4 harmonics of power 30 each, fundamental at
+    (r, z, w) = (1000.25, 3, 10): the stage-4 sub-harmonic max-projection
+    peaks at the 4th harmonic's cell (r = 4001) with about the sum of the
+    four powers there, and stage 1 finds the fundamental."""
+    sig = synth.Signal(1000.25, 3.0, 10.0, 30.0, 0.4)
+    wl = synth.Workload("t", 1 << 13, 20, 2, 60, 20, (1, 4), (20.0, 60.0), 9, [sig], harmonics=4)
+    p = oracle.Params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=(1, 4), thresh=(20.0, 60.0))
+    res = oracle.subharmonic_search(wl.make(), p)
+    M4, arg4 = res.maxproj[4]
+    q = int(np.argmax(M4))
+    assert abs(q - 2 * 4 * sig.r) <= 1
+    zt, wt = oracle.grid(p)
+    assert abs(zt[arg4[q]] - 4 * sig.z) <= 2 and abs(wt[arg4[q]] - 4 * sig.w) <= 20
+    assert 0.6 * 4 * sig.snr < M4[q] < 1.2 * 4 * sig.snr + 10
+    assert any(H == 4 and abs(c - q) <= 1 for H, c, _, _ in res.candidates)
+    M1, _ = res.maxproj[1]
+    assert abs(int(np.argmax(M1[:4000])) - 2 * sig.r) <= 1
