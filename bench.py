@@ -53,7 +53,9 @@ def args_():
     ap.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals")
     ap.add_argument("--workers", type=int, default=4, help="serve: plans sharing the bank")
     ap.add_argument("--dm-count", type=int, default=64)
-    ap.add_argument("--autotune", action="store_true", help="pick the segment length by timing (cached)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the tile shape (segment length, template group size) by timing (cached)")
+    ap.add_argument("--group-size", type=int, default=0, help="templates per template group (0: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seg-len", type=int, default=0)
     ap.add_argument("--stages", default="",
@@ -330,9 +332,11 @@ def dm_bench(a):
     specs = [synth.spectrum(n, seed, sigs) for n, seed, sigs in trials]
     zmax, dz, wmax, dw, stages = 200, 2, 300, 20, (1, 2, 4, 8)
     max_bins = 1 << 23
-    seg_len = autotune.best_seg_len(zmax, dz, wmax, dw, stages, 1 << 21) if a.autotune else 0
+    seg_len, group_size = (autotune.best_shape(zmax, dz, wmax, dw, stages, 1 << 21) if a.autotune
+                           else (a.seg_len, a.group_size))
     p = pkg.make_params(zmax, dz, wmax, dw, stages=stages, thresh=SIGMA_T, thresh_mode=pkg.THRESH_SIGMA,
-                        seg_len=seg_len, max_bins=max_bins, max_candidates=1 << 22, max_batch=16)
+                        seg_len=seg_len, max_bins=max_bins, max_candidates=1 << 22, max_batch=16,
+                        group_size=group_size)
     plan = pkg.Plan(p)
     dev = [torch.from_numpy(s).cuda() for s in specs]
     batches, cur, tot = [], [], 0
@@ -500,9 +504,15 @@ def main():
     import synth
     wl = workload(a.workload, a.bins, a.stages)
     spec = synth.spectrum(wl.n_bins, wl.seed + 1000 * rank, wl.signals) if rank else wl.make()
+    seg_len, group_size = a.seg_len, a.group_size
+    if a.autotune and world == 1:
+        from paper_1911_01353_gb300 import autotune
+        seg_len, group_size = autotune.best_shape(wl.zmax, wl.dz, wl.wmax, wl.dw, wl.stages, wl.n_bins,
+                                                  device=local)
     p = pkg.make_params(wl.zmax, wl.dz, wl.wmax, wl.dw, stages=wl.stages,
                         thresh=SIGMA_T[:len(wl.stages)], thresh_mode=pkg.THRESH_SIGMA,
-                        seg_len=a.seg_len, max_bins=wl.n_bins, max_candidates=1 << 20, precision=a.precision)
+                        seg_len=seg_len, max_bins=wl.n_bins, max_candidates=1 << 20, precision=a.precision,
+                        group_size=group_size)
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
     plan = pkg.Plan(p, device=local, stream=stream)
@@ -642,6 +652,7 @@ def main():
             "config": {"workload": wl.name, "n_bins": wl.n_bins, "templates": plan.info.n_templates,
                        "cells_per_step": cells, "stages": list(wl.stages), "thresh_mode": "sigma",
                        "thresh_T": list(SIGMA_T[:len(wl.stages)]), "seg_len": L, "seg_valid": V,
+                       "group_size": group_size, "n_groups": plan.info.n_groups,
                        "l2": "flushed (256 MB write) before every step",
                        "parallelism": "independent spectra per rank" if world > 1 else "single GPU"},
             "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],

@@ -76,7 +76,10 @@ typedef struct {
     int64_t max_bins;        /* capacity: largest N a search may use (total over a batch), <= 2^29 */
     int64_t max_candidates;  /* capacity of the plan's candidate buffer (total over a batch) */
     int32_t max_batch;       /* largest number of spectra in one jerk_search_batch; 0 = 1 */
-    int32_t reserved;        /* must be 0 */
+    int32_t group_size;      /* templates per template group of the filter (a tile-shape choice:
+                                each group is one work unit of the fused kernel, its bank slice
+                                shared through L2); 0 = choose (32 MiB of bank per group, at
+                                least 8 templates, about 6 waves of CTAs); 1 .. 65536 */
 } jerk_params;
 
 /* One candidate: a peak of the stage-H max-projection over (z, w). */
@@ -323,11 +326,11 @@ jerk_status jerk_plan_info(jerk_plan plan, jerk_info *info);
 /* Where template t (0 <= t < n_templates) sits in the bank: *row is its row
  * of d_bank, *tap_offset the offset bM_g of its group (the spectrum of row
  * `row` is G[f] = (1/L) sum_m c_{m - bM_g} exp(+2 pi i f m / L), m < 2 bM_g + 1,
- * stored as such for precision 1 and 2; for precision 0 the row holds
- * G[f] + G[f + L/2] at f < L/2 and (G[f - L/2] - G[f]) exp(+2 pi i k / R0) at
- * f >= L/2, with R0 = 2^(log2 L mod 4) (16 if that is 1) and
- * k = floor(floor((f - L/2) / (L/16)) / (16/R0)): the FP32 filter's folded
- * form, because the spread spectrum's segments have period L/2) and
+ * stored as such for precision 1 and 2; for precision 0 the row holds, for
+ * f < L/2, G[f] + G[f + L/2] at index 2f and (G[f] - G[f + L/2]) exp(+2 pi i k / R0)
+ * at index 2f + 1, with R0 = 2^(log2 L mod 4) (16 if that is 1) and
+ * k = floor(floor(f / (L/16)) / (16/R0)): the FP32 filter's folded form,
+ * because the spectra of the spread spectrum's segments have period L/2) and
  * *seg_valid its group's segment length V_g = L - 2 bM_g.  Any output may be
  * NULL.  Templates are grouped by half-width m(z, w) so that a group of short
  * filters uses a short overlap. */

@@ -57,18 +57,6 @@ struct ConvCfg {
                                    sizeof(float) * (size_t)SEGS * L + sizeof(uint16_t) * (size_t)SEGS * L;
 };
 
-// sum of 16 values as a balanced tree (short dependency chains)
-__device__ __forceinline__ float tree16(const float (&x)[16]) {
-    float a[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = x[2 * i] + x[2 * i + 1];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = a[2 * i] + a[2 * i + 1];
-    a[0] = a[0] + a[1];
-    a[2] = a[2] + a[3];
-    return a[0] + a[2];
-}
-
 template <int LOG2L, int SIGN>
 __device__ __forceinline__ auto make_tw(const float2 *tab, int j) {
     if constexpr (ConvCfg<LOG2L>::TWS) {
@@ -130,7 +118,6 @@ conv_kernel(ConvArgs a) {
     __shared__ int issued[NBUF];                              // bulk copies issued per buffer
     __shared__ double red[2][32];
     __shared__ double dacc[STATS ? 2 : 1][STATS ? ConvCfg<LOG2L>::THREADS : 1];   // FP64 statistics per thread
-    __shared__ float facc[STATS ? 2 : 1][STATS ? ConvCfg<LOG2L>::THREADS : 1];    // FP32 partial (32 templates)
     __shared__ __align__(16) TplMeta tq[SEGS][4];              // (t, e0, e1) of template k at [k & 3]
     __shared__ __align__(16) RowEntries rent[SEGS][2];         // slot entries of template k at [k & 1]
 
@@ -247,11 +234,10 @@ conv_kernel(ConvArgs a) {
     float mx[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) mx[r] = -1.0f;
+    float fa0 = 0.f, fa1 = 0.f;                               // FP32 statistics partials (32 templates)
     if constexpr (STATS) {
         dacc[0][tid] = 0.0;
         dacc[1][tid] = 0.0;
-        facc[0][tid] = 0.f;
-        facc[1][tid] = 0.f;
     }
     // Template pipeline: template t sits in buffer b = (t - tb) % NBUF; the
     // last segment of the CTA to finish reading a buffer refills it with
@@ -265,9 +251,17 @@ conv_kernel(ConvArgs a) {
         // its values are discarded: the whole segment leaves at the barrier below.
         const bool ok = mbar_wait_bounded(&full[b], (uint32_t)(it / NBUF) & 1u);
         // products with the folded template (sums for m < 8, twiddled
-        // differences for m >= 8), then pass 0 as two half-size DFTs
+        // differences for m >= 8; stored interleaved, one 16-byte load gives
+        // both factors of X[j + NT m]), then pass 0 as two half-size DFTs
+        {
+            const float4 *t4 = reinterpret_cast<const float4 *>(tsm);
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = cmul(xr[m & 7], tsm[j + NT * m]);
+            for (int m = 0; m < 8; ++m) {
+                const float4 g = t4[j + NT * m];
+                v[m] = cmul(xr[m], make_float2(g.x, g.y));
+                v[m + 8] = cmul(xr[m], make_float2(g.z, g.w));
+            }
+        }
         fft_pass0_folded<LOG2L, +1>(v, twi);
         // One barrier per template over the segment's threads: it reports an
         // expired wait, ends this segment's reads of the buffer, and orders the
@@ -348,20 +342,25 @@ conv_kernel(ConvArgs a) {
 #pragma unroll
                     for (int r = 0; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
                 }
-                float c1 = facc[0][tid] + tree16(P);
-                float sq[8];
+                // four independent chains of four cells each, then their sum
+                float a4[4], q4[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) sq[i] = fmaf(P[2 * i], P[2 * i], P[2 * i + 1] * P[2 * i + 1]);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) sq[i] = sq[2 * i] + sq[2 * i + 1];
-                float c2 = facc[1][tid] + ((sq[0] + sq[1]) + (sq[2] + sq[3]));
-                if ((it & 31) == 31) {
-                    dacc[0][tid] += (double)c1;
-                    dacc[1][tid] += (double)c2;
-                    c1 = c2 = 0.f;
+                for (int i = 0; i < 4; ++i) {
+                    a4[i] = P[i];
+                    q4[i] = P[i] * P[i];
                 }
-                facc[0][tid] = c1;
-                facc[1][tid] = c2;
+#pragma unroll
+                for (int r = 4; r < 16; ++r) {
+                    a4[r & 3] += P[r];
+                    q4[r & 3] = fmaf(P[r], P[r], q4[r & 3]);
+                }
+                fa0 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
+                fa1 += (q4[0] + q4[1]) + (q4[2] + q4[3]);
+                if ((it & 31) == 31) {
+                    dacc[0][tid] += (double)fa0;
+                    dacc[1][tid] += (double)fa1;
+                    fa0 = fa1 = 0.f;
+                }
             }
             // harmonic rows of this template: stage the power row now, store it
             // during the next template's transform (whose barriers order it)
@@ -413,8 +412,8 @@ conv_kernel(ConvArgs a) {
             }
         }
         if constexpr (STATS) {
-            double d1 = dacc[0][tid] + (double)facc[0][tid];
-            double d2 = dacc[1][tid] + (double)facc[1][tid];
+            double d1 = dacc[0][tid] + (double)fa0;
+            double d2 = dacc[1][tid] + (double)fa1;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 d1 += __shfl_xor_sync(0xffffffffu, d1, o);

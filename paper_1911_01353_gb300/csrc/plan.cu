@@ -163,6 +163,7 @@ int nseg_for(const jerk_plan_s *pl, int64_t n) {
 }
 
 int tpg_for(const jerk_plan_s *pl, int nseg, int nt) {
+    if (pl->prm.group_size > 0) return std::max(1, std::min(pl->prm.group_size, nt));
     const int64_t target = (int64_t)pl->sms * 6;
     int64_t tpg = ((int64_t)nt * nseg + target - 1) / target;
     const int64_t cap = std::max<int64_t>(1, (int64_t)(kGroupBytes / ((size_t)pl->L * sizeof(float2))));
@@ -242,6 +243,7 @@ jerk_status validate(const jerk_params *p) {
     if (p->max_bins < 1 || p->max_bins > ((int64_t)1 << 29)) return JERK_EINVAL;
     if (p->max_candidates < 1 || p->max_candidates > ((int64_t)1 << 26)) return JERK_EINVAL;
     if (p->max_batch < 0 || p->max_batch > 4096) return JERK_EINVAL;
+    if (p->group_size < 0 || p->group_size > 65536) return JERK_EINVAL;
     if (p->seg_len != 0 && (p->seg_len < 1024 || p->seg_len > 8192 || (p->seg_len & (p->seg_len - 1))))
         return JERK_EINVAL;
     return JERK_OK;

@@ -143,10 +143,12 @@ __global__ void twiddle64_kernel(double2 *tw, int L) {
 // with (its inverse transform's first pass has radix R0 = fold_r0 over the
 // elements f = j + (L/16)(i + (16/R0) k)): the spread segment has zeros at
 // every odd cell, so its spectrum X has period L/2, and that pass splits
-// into two DFTs of R0/2 points on
-//   f < L/2:   G[f] + G[f + L/2],
-//   f >= L/2:  (G[f - L/2] - G[f]) exp(+2 pi i k / R0),  k = ((f - L/2) / (L/16)) / (16 / R0),
-// both computed in FP64 before the one rounding to FP32.
+// into two DFTs of R0/2 points on, for f < L/2,
+//   Ge[f] = G[f] + G[f + L/2],
+//   Go[f] = (G[f] - G[f + L/2]) exp(+2 pi i k / R0),  k = (f / (L/16)) / (16 / R0),
+// both computed in FP64 before the one rounding to FP32 and stored
+// interleaved, row[2 f] = Ge[f], row[2 f + 1] = Go[f], so that one 16-byte
+// shared-memory load gives a thread both factors of its spectrum value X[f].
 __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int32_t *__restrict__ shift,
                                     const int32_t *__restrict__ klen, int K, int L, int log2L,
                                     const double2 *__restrict__ tw, int fold_r0, float2 *__restrict__ bank) {
@@ -187,7 +189,8 @@ __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int3
                 sincospi(2.0 * k / fold_r0, &sw, &cw);
                 v = make_double2(d.x * cw - d.y * sw, d.x * sw + d.y * cw);
             }
-            dst[f] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+            const int slot = f < half ? 2 * f : 2 * (f - half) + 1;
+            dst[slot] = make_float2((float)(v.x * inv), (float)(v.y * inv));
         }
         return;
     }

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("thresh", ctypes.c_float * 4), ("norm_block", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_bins", ctypes.c_int64),
                 ("max_candidates", ctypes.c_int64), ("max_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("group_size", ctypes.c_int32)]
 
 
 class Candidate(ctypes.Structure):
@@ -158,7 +158,7 @@ def _stream_handle(stream):
 
 def make_params(zmax, dz, wmax, dw, stages=(1, 2), thresh=(15.0, 20.0), thresh_mode=THRESH_ABS,
                 pad_bins=16, seg_len=0, norm_block=1024, max_bins=1 << 16, max_candidates=1 << 16,
-                numbetween=2, precision=0, max_batch=1) -> Params:
+                numbetween=2, precision=0, max_batch=1, group_size=0) -> Params:
     p = Params()
     p.zmax, p.dz, p.wmax, p.dw = zmax, dz, wmax, dw
     p.numbetween, p.pad_bins, p.seg_len = numbetween, pad_bins, seg_len
@@ -169,7 +169,7 @@ def make_params(zmax, dz, wmax, dw, stages=(1, 2), thresh=(15.0, 20.0), thresh_m
     p.thresh_mode = thresh_mode
     p.norm_block, p.precision = norm_block, precision
     p.max_bins, p.max_candidates = max_bins, max_candidates
-    p.max_batch, p.reserved = max_batch, 0
+    p.max_batch, p.group_size = max_batch, group_size
     return p
 
 

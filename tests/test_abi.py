@@ -58,14 +58,16 @@ def test_status_strings(L):
 INVALID = [("dz", 0), ("zmax", 21), ("numbetween", 4), ("pad_bins", 0), ("seg_len", 3000),
            ("seg_len", 16384), ("n_stages", 0), ("n_stages", 5), ("norm_block", 5000), ("precision", 3),
            ("precision", -1), ("max_bins", 0), ("max_bins", (1 << 29) + 1), ("max_candidates", 0),
-           ("max_batch", -1), ("thresh_mode", 7), ("zmax", 4098), ("wmax", 32780)]
+           ("max_batch", -1), ("thresh_mode", 7), ("zmax", 4098), ("wmax", 32780), ("group_size", -1),
+           ("group_size", 65537)]
 
 
 def test_valid_params_accepted_without_gpu(L):
     """The validation itself (no device involved) accepts the parameter sets
     the tests and the benchmark use, including the reduced-precision filters."""
     from paper_1911_01353_gb300 import jerk
-    for kw in (dict(), dict(precision=1), dict(precision=2, seg_len=4096), dict(seg_len=8192),
+    for kw in (dict(), dict(precision=1), dict(precision=2, seg_len=4096), dict(seg_len=8192), dict(group_size=1),
+               dict(group_size=65536),
                dict(stages=(1, 2, 4, 8), thresh=(1, 1, 1, 1)), dict(stages=(1, 3), thresh=(1, 1))):
         p = jerk.make_params(20, 2, 60, 20, **kw)
         assert L.jerk_params_validate(ctypes.byref(p)) == jerk.JERK_OK, kw

@@ -105,15 +105,18 @@ def test_taps_paper_scale_sample(pkg):
 
 
 def fold_spectrum(G, L):
-    """The folded form the FP32 filter's bank stores (sums of the two halves of
-    G, then their differences times exp(+2 pi i k / R0), k the element's DFT
-    index in the first inverse pass of radix R0)."""
+    """The folded form the FP32 filter's bank stores: interleaved, the sums of
+    the two halves of G and their differences times exp(+2 pi i k / R0), k
+    the element's DFT index in the first inverse pass of radix R0."""
     log2L = int(round(np.log2(L)))
     R0 = 1 << (log2L % 4) if log2L % 4 else 16
     NT, I0, h = L // 16, 16 // R0, L // 2
     f = np.arange(h)
     k = (f // NT) // I0
-    return np.concatenate([G[:h] + G[h:], (G[:h] - G[h:]) * np.exp(2j * np.pi * k / R0)])
+    out = np.empty(L, dtype=complex)
+    out[0::2] = G[:h] + G[h:]
+    out[1::2] = (G[:h] - G[h:]) * np.exp(2j * np.pi * k / R0)
+    return out
 
 
 @pytest.mark.parametrize("precision,seg_len", [(0, 0), (0, 2048), (0, 8192), (2, 0)])
@@ -224,6 +227,24 @@ def test_search_small(pkg, small):
     assert guarded <= 2
     # the injected chirp at r = 10000.25 is found at stage 1 within half a bin
     assert any(c.stage == 1 and abs(c.r - 10000.25) <= 0.25 for c in cands)
+
+
+@pytest.mark.parametrize("group_size", [1, 7, 64])
+def test_search_small_tile_shapes(pkg, small, group_size):
+    """Other template-group sizes (the autotuner's tile-shape parameter): one
+    template per group, a group size that leaves ragged groups, larger groups;
+    every stage and the candidates against the oracle as in test_search_small."""
+    wl, op, F, res = small
+    tol = PLANE_TOL * res.plane.max()
+    p = jerk_params(op, F.size)
+    p.group_size = group_size
+    with pkg.Plan(p) as plan:
+        assert plan.info.n_groups == -(-op.n_templates // group_size)
+        cands = _search(pkg, plan, F)
+        for si, H in enumerate(op.stages):
+            M, t = plan.maxproj(si)
+            compare_maxproj(M, t, res.maxproj[H][0], res.maxproj[H][1], res.sums[H][1], tol)
+    assert compare_candidates(cands, res, tol) <= 2
 
 
 def test_search_small_sigma_mode(pkg, small):
