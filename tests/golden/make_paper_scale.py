@@ -4,7 +4,7 @@ workload) under tests/golden/.
 Calls only ``oracle`` and ``synth`` (never the CUDA path).  The search runs by
 the oracle's FFT route (``oracle.fft_search``: overlap-and-save with its own
 radix-2 FP64 DFT, one power row at a time), because direct summation over
-2^23 cells x 12 261 templates is out of reach on a CPU.  About half an hour
+2^23 cells x 12 261 templates is out of reach on a CPU.  About 15 minutes
 on 8 cores.  Run from the repository root:
 
     python tests/golden/make_paper_scale.py
