@@ -276,7 +276,7 @@ jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jer
                         const double *h_step, const int32_t *h_half, jerk_refined *h_out, void *stream);
 
 /* (No counterpart in the paper.)  Measure, on `device`, two roofline
- * denominators the filter kernels are judged against: the FP32 FMA rate
+ * denominators of the filter kernels' rooflines: the FP32 FMA rate
  * (every SM busy with independent FMA chains; *fp32_tflops counts 2 flops per
  * FMA) and the L2 read bandwidth (a 64 MB buffer read 20 times with 16-byte
  * loads, *l2_gbs).  Takes about 100 ms; allocates and frees 64 MB. */

@@ -67,6 +67,7 @@ def compare(plan, whole_M, whole_cands, whole_stats, sigma):
 
 
 @pytest.mark.parametrize("mode,stages,thresh,parts", [
+    ("sigma", (1, 2), (6.0, 6.0), 1),
     ("abs", (1, 2), (8.0, 11.0), 2),
     ("sigma", (1, 2, 3), (6.0, 6.0, 5.0), 2),
     ("sigma", (1, 2, 4, 8), (5.0, 5.0, 5.0, 5.0), 3),
