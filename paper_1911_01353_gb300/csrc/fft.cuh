@@ -18,9 +18,9 @@
 
 namespace jerk {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
@@ -45,19 +45,19 @@ struct FftCfg {
 // ---------------------------------------------------------------------------
 
 template <int SIGN>
-__device__ __forceinline__ float2 mul_i(float2 a) {  // (SIGN i) * a
+__host__ __device__ __forceinline__ float2 mul_i(float2 a) {  // (SIGN i) * a
     return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
 template <int SIGN>
-__device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
+__host__ __device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
     float2 s = cadd(a0, a1), d = csub(a0, a1);
     a0 = s;
     a1 = d;
 }
 
 template <int SIGN>
-__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
+__host__ __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
     float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
     float2 s13 = cadd(a1, a3), d13 = mul_i<SIGN>(csub(a1, a3));
     a0 = cadd(s02, s13);
@@ -68,7 +68,7 @@ __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 
 
 // exp(SIGN 2 pi i m / 16) as constants
 template <int SIGN, int M>
-__device__ __forceinline__ float2 w16() {
+__host__ __device__ __forceinline__ float2 w16() {
     constexpr float c[16] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
                              0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f,
                              -1.0f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508977f,
@@ -80,57 +80,113 @@ __device__ __forceinline__ float2 w16() {
     return make_float2(c[M % 16], SIGN > 0 ? s[M % 16] : -s[M % 16]);
 }
 
-// y_r = sum_k a_k exp(SIGN 2 pi i k r / 16): 4 x 4 split, k = k1 + 4 k2, r = r1 + 4 r2.
+// The twiddles exp(SIGN 2 pi i m / 8) with m odd are c (+-1 +- i), c = 1/sqrt 2:
+// a butterfly x0 +- w b with such a w is formed as x0 +- c (u, v), (u, v) the
+// sums and differences of b's parts (eighth_root_parts), with fused
+// multiply-adds -- six instructions where a complex product and two complex
+// additions take eight.
+constexpr float kRsqrt2 = 0.70710678118654752f;
+
+// (u, v) with w b = c (u, v) for w = exp(SIGN 2 pi i M / 8), M = 1 or 3
+template <int SIGN, int M>
+__host__ __device__ __forceinline__ float2 eighth_root_parts(float2 b) {
+    static_assert(M == 1 || M == 3, "odd eighths of a turn below one half");
+    // M = 1: w = c (1 + SIGN i);  M = 3: w = c (-1 + SIGN i)
+    if constexpr (M == 1)
+        return SIGN > 0 ? make_float2(b.x - b.y, b.y + b.x) : make_float2(b.x + b.y, b.y - b.x);
+    else
+        return SIGN > 0 ? make_float2(-b.x - b.y, b.x - b.y) : make_float2(b.y - b.x, -b.y - b.x);
+}
+
+// y_r = sum_k a_k exp(SIGN 2 pi i k r / 16): 4 x 4 split, k = k1 + 4 k2,
+// r = r1 + 4 r2.  Layer 1: C[k1][r1] = DFT4 over k2; layer 2: for each r1, a
+// DFT4 over k1 of C[k1][r1] w16^(k1 r1).  The twiddles w16^2 and w16^6 are
+// formed inside their butterflies (eighth_root_parts), w16^4 = SIGN i is a swap.
 template <int SIGN>
-__device__ __forceinline__ void dft16(float2 (&a)[16]) {
+__host__ __device__ __forceinline__ void dft16(float2 (&a)[16]) {
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(a[k1], a[k1 + 4], a[k1 + 8], a[k1 + 12]);
-    // a[k1 + 4 r1] = C[k1][r1]; twiddle by w16^(k1 r1)
-    a[5] = cmul(a[5], w16<SIGN, 1>());
-    a[9] = cmul(a[9], w16<SIGN, 2>());
-    a[13] = cmul(a[13], w16<SIGN, 3>());
-    a[6] = cmul(a[6], w16<SIGN, 2>());
-    a[10] = mul_i<SIGN>(a[10]);
-    a[14] = cmul(a[14], w16<SIGN, 6>());
-    a[7] = cmul(a[7], w16<SIGN, 3>());
-    a[11] = cmul(a[11], w16<SIGN, 6>());
-    a[15] = cmul(a[15], w16<SIGN, 9>());
-    // (k1 index is the fast one above; a[k1 + 4 r1] with r1 = element / 4)
+    // a[k1 + 4 r1] = C[k1][r1]
+    float2 y[16];
+    // r1 = 0: no twiddles
+    {
+        float2 x0 = a[0], x1 = a[1], x2 = a[2], x3 = a[3];
+        dft4<SIGN>(x0, x1, x2, x3);
+        y[0] = x0;
+        y[4] = x1;
+        y[8] = x2;
+        y[12] = x3;
+    }
+    // r1 = 1: x1 = C1 w^1, x2 = C2 w^2, x3 = C3 w^3
+    {
+        const float2 q = eighth_root_parts<SIGN, 1>(a[6]);         // w^2 C2 = c q
+        const float2 s02 = make_float2(fmaf(kRsqrt2, q.x, a[4].x), fmaf(kRsqrt2, q.y, a[4].y));
+        const float2 d02 = make_float2(fmaf(-kRsqrt2, q.x, a[4].x), fmaf(-kRsqrt2, q.y, a[4].y));
+        const float2 x1 = cmul(a[5], w16<SIGN, 1>()), x3 = cmul(a[7], w16<SIGN, 3>());
+        const float2 s13 = cadd(x1, x3), d13 = mul_i<SIGN>(csub(x1, x3));
+        y[1] = cadd(s02, s13);
+        y[9] = csub(s02, s13);
+        y[5] = cadd(d02, d13);
+        y[13] = csub(d02, d13);
+    }
+    // r1 = 2: x1 = C1 w^2, x2 = C2 w^4 = SIGN i C2, x3 = C3 w^6 = w^2 (SIGN i C3)
+    {
+        const float2 i2 = mul_i<SIGN>(a[10]), i3 = mul_i<SIGN>(a[11]);
+        const float2 s02 = cadd(a[8], i2), d02 = csub(a[8], i2);
+        const float2 e = cadd(a[9], i3), f = csub(a[9], i3);       // x1 + x3 = w^2 e, x1 - x3 = w^2 f
+        const float2 qe = eighth_root_parts<SIGN, 1>(e);            // w^2 e = c qe
+        const float2 qf = mul_i<SIGN>(eighth_root_parts<SIGN, 1>(f));   // SIGN i w^2 f = c qf
+        y[2] = make_float2(fmaf(kRsqrt2, qe.x, s02.x), fmaf(kRsqrt2, qe.y, s02.y));
+        y[10] = make_float2(fmaf(-kRsqrt2, qe.x, s02.x), fmaf(-kRsqrt2, qe.y, s02.y));
+        y[6] = make_float2(fmaf(kRsqrt2, qf.x, d02.x), fmaf(kRsqrt2, qf.y, d02.y));
+        y[14] = make_float2(fmaf(-kRsqrt2, qf.x, d02.x), fmaf(-kRsqrt2, qf.y, d02.y));
+    }
+    // r1 = 3: x1 = C1 w^3, x2 = C2 w^6, x3 = C3 w^9
+    {
+        const float2 q = eighth_root_parts<SIGN, 3>(a[14]);        // w^6 C2 = c q
+        const float2 s02 = make_float2(fmaf(kRsqrt2, q.x, a[12].x), fmaf(kRsqrt2, q.y, a[12].y));
+        const float2 d02 = make_float2(fmaf(-kRsqrt2, q.x, a[12].x), fmaf(-kRsqrt2, q.y, a[12].y));
+        const float2 x1 = cmul(a[13], w16<SIGN, 3>()), x3 = cmul(a[15], w16<SIGN, 9>());
+        const float2 s13 = cadd(x1, x3), d13 = mul_i<SIGN>(csub(x1, x3));
+        y[3] = cadd(s02, s13);
+        y[11] = csub(s02, s13);
+        y[7] = cadd(d02, d13);
+        y[15] = csub(d02, d13);
+    }
 #pragma unroll
-    for (int r1 = 0; r1 < 4; ++r1) dft4<SIGN>(a[4 * r1], a[4 * r1 + 1], a[4 * r1 + 2], a[4 * r1 + 3]);
-    // now a[r2 + 4 r1] = y[r1 + 4 r2]; transpose the 4x4 register block
-    float2 t;
-    t = a[1]; a[1] = a[4]; a[4] = t;
-    t = a[2]; a[2] = a[8]; a[8] = t;
-    t = a[3]; a[3] = a[12]; a[12] = t;
-    t = a[6]; a[6] = a[9]; a[9] = t;
-    t = a[7]; a[7] = a[13]; a[13] = t;
-    t = a[11]; a[11] = a[14]; a[14] = t;
+    for (int i = 0; i < 16; ++i) a[i] = y[i];
 }
 
 // y_r = sum_k a_k exp(SIGN 2 pi i k r / 8): k = k1 + 2 k2, r = r1 + 4 r2.
 template <int SIGN>
-__device__ __forceinline__ void dft8(float2 (&a)[8]) {
+__host__ __device__ __forceinline__ void dft8(float2 (&a)[8]) {
     dft4<SIGN>(a[0], a[2], a[4], a[6]);   // k1 = 0 -> C[0][r1] at a[2 r1]
     dft4<SIGN>(a[1], a[3], a[5], a[7]);   // k1 = 1 -> C[1][r1] at a[2 r1 + 1]
-    a[3] = cmul(a[3], w16<SIGN, 2>());    // w8^1
-    a[5] = mul_i<SIGN>(a[5]);             // w8^2
-    a[7] = cmul(a[7], w16<SIGN, 6>());    // w8^3
-#pragma unroll
-    for (int r1 = 0; r1 < 4; ++r1) dft2<SIGN>(a[2 * r1], a[2 * r1 + 1]);
-    // a[r2 + 2 r1] = y[r1 + 4 r2] -> natural order
+    // per r1: y[r1] = C0 + w8^r1 C1, y[r1 + 4] = C0 - w8^r1 C1
     float2 y[8];
-#pragma unroll
-    for (int r1 = 0; r1 < 4; ++r1) {
-        y[r1] = a[2 * r1];
-        y[r1 + 4] = a[2 * r1 + 1];
+    y[0] = cadd(a[0], a[1]);
+    y[4] = csub(a[0], a[1]);
+    {
+        const float2 q = eighth_root_parts<SIGN, 1>(a[3]);          // w8^1 C1 = c q
+        y[1] = make_float2(fmaf(kRsqrt2, q.x, a[2].x), fmaf(kRsqrt2, q.y, a[2].y));
+        y[5] = make_float2(fmaf(-kRsqrt2, q.x, a[2].x), fmaf(-kRsqrt2, q.y, a[2].y));
+    }
+    {
+        const float2 t = mul_i<SIGN>(a[5]);                          // w8^2 = SIGN i
+        y[2] = cadd(a[4], t);
+        y[6] = csub(a[4], t);
+    }
+    {
+        const float2 q = eighth_root_parts<SIGN, 3>(a[7]);          // w8^3 C1 = c q
+        y[3] = make_float2(fmaf(kRsqrt2, q.x, a[6].x), fmaf(kRsqrt2, q.y, a[6].y));
+        y[7] = make_float2(fmaf(-kRsqrt2, q.x, a[6].x), fmaf(-kRsqrt2, q.y, a[6].y));
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) a[i] = y[i];
 }
 
 template <int SIGN, int R>
-__device__ __forceinline__ void dft_small(float2 (&b)[R]) {
+__host__ __device__ __forceinline__ void dft_small(float2 (&b)[R]) {
     if constexpr (R == 1) {
         // one point: its own transform
     } else if constexpr (R == 2) {
