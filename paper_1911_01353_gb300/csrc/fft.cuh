@@ -245,8 +245,11 @@ struct FftTw {
 
 // Twiddle factors read from tables in shared memory (built once per CTA by
 // twiddle_tables below), for the inverse (SIGN = +1) or, conjugated, the
-// forward transform.  Table 0: w_L^{f1 r} at [(r-1) * N0 + f1];
-// table s (1..NP-1): w_{N_{s-1}}^{f' r} at [(r-1) * N_s + f'].
+// forward transform.  Table 0: w_L^{f1 r} at [(r-1) * N0 + f1], or, when pass
+// 0 has radix 16, in pairs (r, r + 1) for r = 1, 3, .., 15 as float4 [(r-1)/2]
+// [f1] (one 16-byte load per two factors; the last pair's second half is
+// padding); table s (1..NP-1): w_{N_{s-1}}^{f' r} in pairs (r, r + 1) as float4
+// [(r-1)/2][f'] the same way.
 template <int LOG2L, int SIGN>
 struct FftTwSmem {
     using C = FftCfg<LOG2L>;
@@ -256,17 +259,31 @@ struct FftTwSmem {
     __device__ __forceinline__ static float2 cj(float2 w) { return SIGN > 0 ? w : make_float2(w.x, -w.y); }
     template <int R>
     __device__ __forceinline__ void apply0(float2 *b, int i) const {
-        const float2 *p = t0 + j + C::NT * i;
+        if constexpr (R == 16) {
+            const float4 *p4 = reinterpret_cast<const float4 *>(t0) + j;
 #pragma unroll
-        for (int r = 1; r < R; ++r) b[r] = cmul(b[r], cj(p[(r - 1) * C::N0]));
+            for (int k = 0; k < 8; ++k) {
+                const float4 w = p4[k * C::N0];
+                b[2 * k + 1] = cmul(b[2 * k + 1], cj(make_float2(w.x, w.y)));
+                if (k < 7) b[2 * k + 2] = cmul(b[2 * k + 2], cj(make_float2(w.z, w.w)));
+            }
+        } else {
+            const float2 *p = t0 + j + C::NT * i;
+#pragma unroll
+            for (int r = 1; r < R; ++r) b[r] = cmul(b[r], cj(p[(r - 1) * C::N0]));
+        }
     }
     __device__ __forceinline__ void applys(float2 *a, int s) const {
         int ns = C::N0;
 #pragma unroll
         for (int q = 0; q < s; ++q) ns /= 16;
-        const float2 *p = ts[s - 1] + (j & (ns - 1));
+        const float4 *p4 = reinterpret_cast<const float4 *>(ts[s - 1]) + (j & (ns - 1));
 #pragma unroll
-        for (int r = 1; r < 16; ++r) a[r] = cmul(a[r], cj(p[(r - 1) * ns]));
+        for (int k = 0; k < 8; ++k) {
+            const float4 w = p4[k * ns];
+            a[2 * k + 1] = cmul(a[2 * k + 1], cj(make_float2(w.x, w.y)));
+            if (k < 7) a[2 * k + 2] = cmul(a[2 * k + 2], cj(make_float2(w.z, w.w)));
+        }
     }
 };
 
@@ -274,11 +291,11 @@ struct FftTwSmem {
 template <int LOG2L>
 __host__ __device__ constexpr int twiddle_table_elems() {
     using C = FftCfg<LOG2L>;
-    int n = (C::R0 - 1) * C::N0;
+    int n = C::R0 == 16 ? 16 * C::N0 : (C::R0 - 1) * C::N0;
     int ns = C::N0;
     for (int s = 1; s < C::NP; ++s) {
         ns /= 16;
-        n += 15 * ns;
+        n += 16 * ns;
     }
     return n;
 }
@@ -287,20 +304,28 @@ __host__ __device__ constexpr int twiddle_table_elems() {
 template <int LOG2L>
 __device__ __forceinline__ void fill_twiddle_tables(float2 *tab, int tid, int nthr) {
     using C = FftCfg<LOG2L>;
-    for (int e = tid; e < (C::R0 - 1) * C::N0; e += nthr) {
-        const int r = e / C::N0 + 1, f1 = e % C::N0;
-        tab[e] = unit_root<+1>((f1 * r) & (C::L - 1), C::L);
+    if constexpr (C::R0 == 16) {
+        // pairs (r, r + 1), r = 1, 3, .., 15, as float4 [k][f1] (k = (r - 1) / 2); r = 16 is padding
+        for (int e = tid; e < 16 * C::N0; e += nthr) {
+            const int k = e / (2 * C::N0), rem = e % (2 * C::N0), f1 = rem >> 1, r = 2 * k + 1 + (rem & 1);
+            tab[e] = r < 16 ? unit_root<+1>((f1 * r) & (C::L - 1), C::L) : make_float2(1.f, 0.f);
+        }
+    } else {
+        for (int e = tid; e < (C::R0 - 1) * C::N0; e += nthr) {
+            const int r = e / C::N0 + 1, f1 = e % C::N0;
+            tab[e] = unit_root<+1>((f1 * r) & (C::L - 1), C::L);
+        }
     }
-    float2 *p = tab + (C::R0 - 1) * C::N0;
+    float2 *p = tab + (C::R0 == 16 ? 16 * C::N0 : (C::R0 - 1) * C::N0);
     int nprev = C::N0;
 #pragma unroll
     for (int s = 1; s < C::NP; ++s) {
         const int ns = nprev / 16;
-        for (int e = tid; e < 15 * ns; e += nthr) {
-            const int r = e / ns + 1, fp = e % ns;
-            p[e] = unit_root<+1>((fp * r) & (nprev - 1), nprev);
+        for (int e = tid; e < 16 * ns; e += nthr) {
+            const int k = e / (2 * ns), rem = e % (2 * ns), fp = rem >> 1, r = 2 * k + 1 + (rem & 1);
+            p[e] = r < 16 ? unit_root<+1>((fp * r) & (nprev - 1), nprev) : make_float2(1.f, 0.f);
         }
-        p += 15 * ns;
+        p += 16 * ns;
         nprev = ns;
     }
 }
@@ -311,13 +336,13 @@ __device__ __forceinline__ FftTwSmem<LOG2L, SIGN> bind_twiddle_tables(const floa
     FftTwSmem<LOG2L, SIGN> tw;
     tw.j = j;
     tw.t0 = tab;
-    const float2 *p = tab + (C::R0 - 1) * C::N0;
+    const float2 *p = tab + (C::R0 == 16 ? 16 * C::N0 : (C::R0 - 1) * C::N0);
     int ns = C::N0;
 #pragma unroll
     for (int s = 1; s < C::NP; ++s) {
         ns /= 16;
         tw.ts[s - 1] = p;
-        p += 15 * ns;
+        p += 16 * ns;
     }
     return tw;
 }
