@@ -1,5 +1,6 @@
 """Helper of test_gpu_checks.py (not a test module): run a fixed set of
-searches through the library loaded by the binding and print, as one JSON
+searches (single, batched, sub-grid, split by template range) and plane rows
+through the library loaded by the binding and print, as one JSON
 line, their candidates and the plan's bounds-check counters.  Run with
 JERK_CHECKS=1 it uses the debug build, whose kernels check the indices of
 their global stores and copies."""
@@ -40,6 +41,20 @@ def main():
             out["runs"]["batch%d" % prec] = key(plan.candidates())
             plan.search_batch([torch.from_numpy(G).cuda()], zmax=[8], wmax=[60])
             out["runs"]["grid%d" % prec] = key(plan.candidates())
+            # one search split in two template ranges, merged (as ranks would merge it)
+            x = torch.from_numpy(F).cuda()
+            T = plan.info.n_templates
+            merged, tot = None, np.zeros((3, 4))
+            for lo, hi in ((0, T // 2), (T // 2, T)):
+                plan.search_range(x, lo, hi)
+                tot += np.stack(plan.range_sums())
+                parts = [plan.maxproj_tensor(si).clone() for si in range(4)]
+                merged = parts if merged is None else [torch.maximum(a, b) for a, b in zip(merged, parts)]
+            for si in range(4):
+                plan.maxproj_tensor(si).copy_(merged[si])
+            torch.cuda.synchronize()
+            plan.select(tot[0], tot[1], tot[2])
+            out["runs"]["split%d" % prec] = key(plan.candidates())
             rows = torch.empty((3, 2 * n), dtype=torch.float32, device="cuda")
             plan.plane(torch.from_numpy(F).cuda(), 10, 3, rows)
             r = rows.cpu().numpy()

@@ -1,5 +1,6 @@
 """The debug build's bounds checks (jerk_check_counts): searches, batches,
-sub-grid batches and plane rows of both filters, run through the library
+sub-grid batches, searches split by template range and plane rows of both
+filters, run through the library
 built with -DJERK_CHECKS, make no out-of-range global store or copy, and give
 the same candidates and plane rows as the release library.  The release
 library reports its checks absent."""
@@ -41,3 +42,5 @@ def test_bounds_checked_build_is_clean_and_equal():
     for name in chk["runs"]:
         assert chk["runs"][name] == rel["runs"][name], name
     assert chk["runs"]["search0"], "the workload has candidates"
+    for prec in (0, 2):
+        assert chk["runs"]["split%d" % prec] == chk["runs"]["search%d" % prec], prec
