@@ -92,6 +92,23 @@ def test_ranges_merged_equal_whole_bank(pkg, mode, stages, thresh, parts):
         assert [(c.stage, c.p, c.t) for c in plan.candidates()] == [(c.stage, c.p, c.t) for c in whole_cands]
 
 
+def test_uneven_ranges(pkg):
+    """Ranges of very different sizes (one template, a few, the rest) merge to
+    the whole search as well."""
+    wl = synth.small_single()
+    op = oracle_params(wl, mode="sigma", thresh=(6.0, 6.0))
+    F = wl.make()
+    x = torch.from_numpy(F).cuda()
+    with pkg.Plan(jerk_params(op, F.size)) as plan:
+        plan.search(x)
+        whole_cands = plan.candidates()
+        whole_M = [plan.maxproj(si) for si in range(2)]
+        whole_stats = plan.stats()
+        T = plan.info.n_templates
+        split_search(plan, x, [(0, 1), (1, 10), (10, 73), (73, T)])
+        compare(plan, whole_M, whole_cands, whole_stats, True)
+
+
 def test_range_call_order(pkg):
     from paper_1911_01353_gb300 import jerk
     wl = synth.small_single()
