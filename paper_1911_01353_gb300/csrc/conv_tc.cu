@@ -83,35 +83,39 @@ __device__ __forceinline__ uint32_t idesc() {
     return (1u << 4) | (t << 7) | (t << 10) | ((A_MN ? 1u : 0u) << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// D[128 x 128] (tensor memory) = A[128 x 128] B[128 x 128], 8 steps of K = 16
+// One K = 16 step s (0..7) of D[128 x 128] (tensor memory) = A[128 x 128]
+// B[128 x 128], issued by one elected lane of the calling warp: the whole warp
+// executes it, so no lane diverges around the issue.  `ad` and `bd` are the
+// step-0 descriptors; step s starts 2 LBO bytes further along K, 16 in the
+// descriptor's 16-byte address field (which cannot carry: shared addresses
+// are below 2^18).
 template <int PREC, bool A_MN>
-__device__ __forceinline__ void mma_tile(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr) {
-    const uint32_t id = idesc<PREC, A_MN>();
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        const uint64_t ad = sdesc(a_addr + s * 2 * LBO), bd = sdesc(b_addr + s * 2 * LBO);
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(ad), "l"(bd), "r"(id), "r"((uint32_t)(s > 0))
-            : "memory");
-    }
-}
-
-// one K = 16 step s (0..7) of that product
-template <int PREC, bool A_MN>
-__device__ __forceinline__ void mma_step(uint32_t d_tmem, uint32_t a_addr, uint32_t b_addr, int s) {
-    const uint64_t ad = sdesc(a_addr + s * 2 * LBO), bd = sdesc(b_addr + s * 2 * LBO);
+__device__ __forceinline__ void mma_step_warp(uint32_t d_tmem, uint64_t ad, uint64_t bd, int s) {
+    const uint64_t step = (uint64_t)(s * (2 * LBO >> 4));
     asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(ad), "l"(bd), "r"(idesc<PREC, A_MN>()), "r"((uint32_t)(s > 0))
+        "{\n\t.reg .pred e, p;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(ad + step), "l"(bd + step), "r"(idesc<PREC, A_MN>()), "r"((uint32_t)(s > 0))
         : "memory");
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+// all eight steps
+template <int PREC, bool A_MN>
+__device__ __forceinline__ void mma_tile_warp(uint32_t d_tmem, uint64_t ad, uint64_t bd) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) mma_step_warp<PREC, A_MN>(d_tmem, ad, bd, s);
+}
+
+// the elected lane's products so far arrive on `bar` when they complete
+__device__ __forceinline__ void mma_commit_warp(uint64_t *bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -156,6 +160,8 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     __shared__ int xmax_bits[SEGS];
     __shared__ double red[2][THREADS / 32];
     __shared__ double dacc[STATS ? 2 : 1][STATS ? THREADS : 1];
+    __shared__ __align__(16) TplMeta tq[4];                 // (t, e0, e1) of template k at [k & 3]
+    __shared__ __align__(16) RowEntries rent[2];            // slot entries of template k at [k & 1]
 
     const int tid = threadIdx.x;
     const int half = tid / NT, j = tid % NT;                  // forward-transform mapping
@@ -249,6 +255,25 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             if (lane == 0) atomicMax(&xmax_bits[s2], __float_as_int(m[s2]));   // non-negative: int order = float order
         }
     }
+    if (tid == 64 && tb < te) {
+        // the metadata pipeline's first stages: (t, e0, e1) of the first two
+        // templates, t of the third, the slot entries of the first (later ones
+        // are prefetched by cp.async in the loop)
+        // (plane mode needs t only: it has no slot tables)
+        for (int q = 0; q < 3 && tb + q < te; ++q) {
+            const int t = __ldg(a.order + tb + q);
+            const bool ent = MODE == 0 && q < 2;
+            tq[(tb + q) & 3] = TplMeta{t, ent ? __ldg(a.slot_beg + t) : 0, ent ? __ldg(a.slot_beg + t + 1) : 0, 0};
+        }
+        if constexpr (MODE == 0) {
+            const TplMeta m0 = tq[tb & 3];
+            for (int i = 0; i < m0.e1 - m0.e0; ++i) {
+                rent[tb & 1].h[i] = __ldg(a.slot_h + m0.e0 + i);
+                rent[tb & 1].off[i] = __ldg(itm->slot_off + m0.e0 + i);
+                rent[tb & 1].len[i] = __ldg(itm->slot_len + m0.e0 + i);
+            }
+        }
+    }
     __syncthreads();                                          // the work buffers are free from here
     if (tid == 0)
         for (int b = 0; b < 2 && tb + b < te; ++b) {
@@ -269,13 +294,15 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         }
     }
 
-    // cells of this thread: n = 64 (16 gcol + i) + r of segment seg
+    // cells of this thread: n = 64 (16 gcol + i) + r of segment seg.  n grows
+    // with i, so the valid ones (n < V and within the spectrum) are the first
+    // nvalid.
     const int seg0 = (s_base + seg) * V;
-    unsigned vmask = 0;
+    int nvalid = 0;
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
         const int n = 64 * (16 * gcol + i) + r;
-        if (n < V && seg0 + n < bN) vmask |= 1u << i;
+        nvalid += (n < V && seg0 + n < bN) ? 1 : 0;
     }
     float mx[16];
 #pragma unroll
@@ -289,22 +316,25 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     const uint32_t a1_r0 = smem_u32(sm + OFF_A1) + (ka >> 3) * SBO + (ka & 7) * 16 + blk * LBO;
     const uint32_t a1_r1 = a1_r0 + 8 * SBO;
     const uint32_t a3_col = smem_u32(sm + OFF_A3) + (r >> 3) * LBO + (r & 7) * 16 + (8 * seg + 2 * gcol) * SBO;
-    const float2 *twt = reinterpret_cast<const float2 *>(sm + OFF_TW);
+    const float2 *twt = reinterpret_cast<const float2 *>(sm + OFF_TW) + 16 * 64 * gcol + r;
+    uint16_t *amx_t = amx_s + seg * L + 64 * 16 * gcol + r;   // this thread's cells, stride 64
 
     // ---- the three thread phases of one template --------------------------------
-    // The issuing thread (tid 0) interleaves the eight K steps of the product it
-    // launches with its own share of a phase: tcgen05.mma blocks while the
-    // tensor core's queue is full, so one step per slice of work keeps its warp
-    // from stalling for the whole product.
-    const uint32_t sA1 = smem_u32(sm + OFF_A1), sA3 = smem_u32(sm + OFF_A3), sB = smem_u32(sm + OFF_B);
+    // Warp 0 issues the products (one elected lane, so the warp never diverges
+    // around an issue) and interleaves their eight K steps with its own share
+    // of a phase: tcgen05.mma blocks while the tensor core's queue is full, so
+    // one step per slice of work keeps the warp from stalling for a whole
+    // product.
+    const uint64_t dA1 = sdesc(smem_u32(sm + OFF_A1)), dA3 = sdesc(smem_u32(sm + OFF_A3)),
+                   dB = sdesc(smem_u32(sm + OFF_B));
     // A: Z = X C (scaled) -> A1 (K-major), from ring buffer `b`; issues step 3
-    // of the previous template when `issue3`
+    // of the previous template when `issue3` (warp-uniform)
     auto phase_a = [&](int b, bool issue3) {
-        const float2 *C = ring + b * L;
+        const float2 *C = ring + b * L + ka + 64 * 8 * blk;
         uint32_t pr[8], pi[8];                                // [seg 0: 0..3 | seg 1: 4..7]
 #pragma unroll
         for (int i = 0; i < 8; i += 2) {
-            const float2 c0 = C[ka + 64 * (8 * blk + i)], c1 = C[ka + 64 * (8 * blk + i + 1)];
+            const float2 c0 = C[64 * i], c1 = C[64 * (i + 1)];
 #pragma unroll
             for (int s2 = 0; s2 < SEGS; ++s2) {
                 const float2 z0 = cmul(xa[s2][i], c0), z1 = cmul(xa[s2][i + 1], c1);
@@ -312,11 +342,11 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 pi[4 * s2 + (i >> 1)] = pack2<PREC>(z0.y, z1.y);
             }
             if (issue3) {
-                mma_step<PREC, true>(tmem + 128, sA3, sB, i);
-                mma_step<PREC, true>(tmem + 128, sA3, sB, i + 1);
+                mma_step_warp<PREC, true>(tmem + 128, dA3, dB, i);
+                mma_step_warp<PREC, true>(tmem + 128, dA3, dB, i + 1);
             }
         }
-        if (issue3) mma_commit(&mbar3);
+        if (issue3) mma_commit_warp(&mbar3);
         sts128(a1_r0, pr, 0);
         sts128(a1_r0 + 8 * LBO, pi, 0);
         sts128(a1_r1, pr, 4);
@@ -330,8 +360,8 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         uint32_t pr[8], pi[8];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-            const float2 u0 = cmul(make_float2(ur[i], ui[i]), twt[(16 * gcol + i) * 64 + r]);
-            const float2 u1 = cmul(make_float2(ur[i + 1], ui[i + 1]), twt[(16 * gcol + i + 1) * 64 + r]);
+            const float2 u0 = cmul(make_float2(ur[i], ui[i]), twt[i * 64]);
+            const float2 u1 = cmul(make_float2(ur[i + 1], ui[i + 1]), twt[(i + 1) * 64]);
             pr[i >> 1] = pack2<PREC>(u0.x, u1.x);
             pi[i >> 1] = pack2<PREC>(u0.y, u1.y);
         }
@@ -341,9 +371,10 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         sts128(a3_col + 8 * LBO + SBO, pi, 4);
     };
     // E: D3 -> power, running max, statistics, harmonic rows (search) or plane
-    // rows; issues step 1 of the next template when `issue1`.  The running max
-    // and the statistics use |y|^2 before the segment's power scale psc (a
-    // monotone factor), applied when they leave the CTA.
+    // rows; issues step 1 of the next template when `issue1` (warp-uniform).
+    // The running max and the statistics use |y|^2 before the segment's power
+    // scale psc (a monotone factor), applied when they leave the CTA.  The max
+    // runs over all 16 cells: those past nvalid are never read back.
     auto phase_e = [&](int k, int it, bool issue1) {
         float yr[16], yi[16];
         tmem_ld16(tmem + tlane + 128 + 16 * gcol, yr);
@@ -351,23 +382,34 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         float P[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) P[i] = fmaf(yr[i], yr[i], yi[i] * yi[i]);
-        const int t = __ldg(a.order + k);
+        const int t = tq[k & 3].t;
         if constexpr (MODE == 0) {
-            float s1 = 0.f, s2 = 0.f;
-            const bool all = vmask == 0xFFFFu;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                // cells outside the segment's valid range count as 0 (never read back)
-                const float pm = (all || ((vmask >> i) & 1u)) ? P[i] : 0.f;
-                const bool up = pm > mx[i];
-                mx[i] = up ? pm : mx[i];
-                if (up) amx_s[seg * L + 64 * (16 * gcol + i) + r] = (uint16_t)it;
-                s1 += pm;
-                s2 = fmaf(pm, pm, s2);
-                if (issue1 && (i & 1)) mma_step<PREC, false>(tmem, sA1, sB, i >> 1);
+                if (P[i] > mx[i]) {
+                    mx[i] = P[i];
+                    amx_t[64 * i] = (uint16_t)it;             // rare after the first templates
+                }
+                if (issue1 && (i & 1)) mma_step_warp<PREC, false>(tmem, dA1, dB, i >> 1);
             }
-            if (issue1) mma_commit(&mbar1);
+            if (issue1) mma_commit_warp(&mbar1);
             if constexpr (STATS) {
+                float s1 = 0.f, s2 = 0.f;
+                if (nvalid == 16) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        s1 += P[i];
+                        s2 = fmaf(P[i], P[i], s2);
+                    }
+                } else {
+                    // cells outside the segment's valid range count as 0
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float pm = i < nvalid ? P[i] : 0.f;
+                        s1 += pm;
+                        s2 = fmaf(pm, pm, s2);
+                    }
+                }
                 c1 += s1;
                 c2 += s2;
                 if ((it & 31) == 31) {
@@ -376,33 +418,35 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                     c1 = c2 = 0.f;
                 }
             }
-            // harmonic rows: cell q = seg0 + 64 (16 gcol + i) + r is harmonic h of
-            // fundamental cell q / h when h | q; quotient and remainder are stepped
-            // by 64 per i, so only one division per entry
-            const int e0 = __ldg(a.slot_beg + t), e1 = __ldg(a.slot_beg + t + 1);
-            for (int e = e0; e < e1; ++e) {
-                const int h = __ldg(a.slot_h + e);
-                const int64_t off = __ldg(itm->slot_off + e);
-                float *dst = a.slots + off;
-                const int len = (int)__ldg(itm->slot_len + e);
-                const int q0 = seg0 + 64 * 16 * gcol + r;
+            // harmonic rows: cell q = q0 + 64 i (q0 = seg0 + 1024 gcol + r) is
+            // harmonic h of fundamental cell q / h when h | q
+            const RowEntries &en = rent[k & 1];
+            const int ne = tq[k & 3].e1 - tq[k & 3].e0;
+            const int q0 = seg0 + 1024 * gcol + r;
+            for (int e = 0; e < ne; ++e) {
+                const int h = en.h[e];
+                float *dst = a.slots + en.off[e];
+                const int len = (int)en.len[e];
                 int quo = q0 / h, rem = q0 - quo * h;
-                const int dq = 64 / h, dr = 64 - dq * h;
-                if (dr == 0) {
-                    // h divides 64 (h = 1, 2, 4, 8): the thread's cells are all
-                    // harmonics of this h, or none is
+                if ((64 % h) == 0) {
+                    // h divides 64 (h = 1, 2, 4, 8): all of this thread's cells
+                    // are harmonics of this h, or none is; cell i goes to row
+                    // position quo + i dq while that is below len
                     if (rem == 0) {
+                        const int dq = 64 / h;
+                        const int iend = quo >= len ? 0 : min(nvalid, (len - quo + dq - 1) / dq);
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (((vmask >> i) & 1u) && quo + i * dq < len &&
-                                JERK_CHECK(off + quo + i * dq < a.slot_cap, a.chk, kChkTcRowStore))
+                            if (i < iend && JERK_CHECK(en.off[e] + quo + i * dq < a.slot_cap, a.chk, kChkTcRowStore))
                                 dst[quo + i * dq] = P[i] * psc;
                     }
                 } else {
+                    // quotient and remainder stepped by 64 per cell
+                    const int dq = 64 / h, dr = 64 - dq * h;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        if (((vmask >> i) & 1u) && rem == 0 && quo < len &&
-                            JERK_CHECK(off + quo < a.slot_cap, a.chk, kChkTcRowStore))
+                        if (i < nvalid && rem == 0 && quo < len &&
+                            JERK_CHECK(en.off[e] + quo < a.slot_cap, a.chk, kChkTcRowStore))
                             dst[quo] = P[i] * psc;
                         quo += dq;
                         rem += dr;
@@ -415,16 +459,15 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             }
         } else {
             if (issue1) {
-#pragma unroll
-                for (int s8 = 0; s8 < 8; ++s8) mma_step<PREC, false>(tmem, sA1, sB, s8);
-                mma_commit(&mbar1);
+                mma_tile_warp<PREC, false>(tmem, dA1, dB);
+                mma_commit_warp(&mbar1);
             }
             if (t >= a.t0 && t < a.t0 + a.nt) {
                 const int64_t row0 = (int64_t)(t - a.t0) * bN + seg0;
                 float *prow = a.plane + row0;
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    if (((vmask >> i) & 1u) &&
+                    if (i < nvalid &&
                         JERK_CHECK(row0 + 64 * (16 * gcol + i) + r < a.plane_len, a.chk, kChkTcPlaneStore))
                         prow[64 * (16 * gcol + i) + r] = P[i] * psc;
             }
@@ -443,10 +486,10 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         if (!fail) phase_a(0, false);
         fence_async_smem();
         fail = __syncthreads_or(fail);
-        if (!fail && tid == 0) {
+        if (!fail && warp == 0) {
             tc_fence_after();
-            mma_tile<PREC, false>(tmem, sA1, sB);
-            mma_commit(&mbar1);
+            mma_tile_warp<PREC, false>(tmem, dA1, dB);
+            mma_commit_warp(&mbar1);
         }
         if (!fail && tid == 32 && nt > 2) {                    // buffer 0 is read: template 2 next
             issued[0] += 1;
@@ -460,20 +503,47 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         fail = __any_sync(0xffffffffu, fail);
         tc_fence_after();
         if (!fail) phase_c();
+        if (warp == 2) cp_async_wait_all();                   // the metadata issued last template
         tc_fence_before();
         fence_async_smem();
         if (__syncthreads_or(fail)) {
             fail = true;
             break;
         }
+        if (warp == 2) {
+            // Metadata pipeline (no L2-latency load between a product and the
+            // epilogue that needs it): t of template k + 3, then (e0, e1) of
+            // k + 2, then the slot entries of k + 1.  Every thread is past E of
+            // the previous template, the last reader of the slots written here.
+            const int k = tb + it;
+            if (lane == 0) {
+                if (k + 3 < te) cp_async<4>(&tq[(k + 3) & 3].t, a.order + k + 3);
+                if (MODE == 0 && k + 2 < te) {
+                    const int t2 = tq[(k + 2) & 3].t;
+                    cp_async<4>(&tq[(k + 2) & 3].e0, a.slot_beg + t2);
+                    cp_async<4>(&tq[(k + 2) & 3].e1, a.slot_beg + t2 + 1);
+                }
+            }
+            if (MODE == 0 && k + 1 < te) {
+                const TplMeta m1 = tq[(k + 1) & 3];
+                if (lane < m1.e1 - m1.e0) {
+                    const int e = m1.e0 + lane;
+                    RowEntries &en = rent[(k + 1) & 1];
+                    cp_async<4>(&en.h[lane], a.slot_h + e);
+                    cp_async<8>(&en.off[lane], itm->slot_off + e);
+                    cp_async<8>(&en.len[lane], itm->slot_len + e);
+                }
+            }
+            cp_async_commit();
+        }
         const bool more = it + 1 < nt;
         if (more) {
             // A(it + 1) while step 3 of template it runs
             const int b = (it + 1) & 1;
-            if (tid == 0) tc_fence_after();
+            if (warp == 0) tc_fence_after();
             fail = !mbar_wait_bounded(&full[b], (uint32_t)((it + 1) >> 1) & 1u);
             fail = __any_sync(0xffffffffu, fail);
-            if (!fail) phase_a(b, tid == 0);
+            if (!fail) phase_a(b, warp == 0);
             fence_async_smem();
             if (__syncthreads_or(fail)) {
                 fail = true;
@@ -484,19 +554,20 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 bulk_load(ring + b * L, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + it + 3) * L,
                           (uint32_t)(L * sizeof(float2)), &full[b]);
             }
-            if (tid == 0) tc_fence_after();
-        } else if (tid == 0) {
+            if (warp == 0) tc_fence_after();
+        } else if (warp == 0) {
             tc_fence_after();
-            mma_tile<PREC, true>(tmem + 128, sA3, sB);
-            mma_commit(&mbar3);
+            mma_tile_warp<PREC, true>(tmem + 128, dA3, dB);
+            mma_commit_warp(&mbar3);
         }
         // E(it): step 3 of template it has landed in D3; step 1 of it + 1 runs meanwhile
         fail = !mbar_wait_bounded(&mbar3, (uint32_t)it & 1u);
         fail = __any_sync(0xffffffffu, fail);
         tc_fence_after();
-        if (!fail) phase_e(tb + it, it, more && tid == 0);
+        if (!fail) phase_e(tb + it, it, more && warp == 0);
         tc_fence_before();
     }
+    if (warp == 2) cp_async_wait_all();                       // no copy in flight past the loop
     fail = __syncthreads_or(fail);
 
     // ---- epilogue -----------------------------------------------------------------
@@ -506,7 +577,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             unsigned long long *M1 = itm->M1;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                if ((vmask >> i) & 1u) {
+                if (i < nvalid) {
                     const int n = 64 * (16 * gcol + i) + r;
                     const int tw = __ldg(a.order + tb + amx_s[seg * L + n]);
                     const unsigned long long packed = ((unsigned long long)__float_as_uint(mx[i] * psc) << 32) |
