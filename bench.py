@@ -97,7 +97,7 @@ def conv_flops_per_cell(L, V):
 
 def kernel_hash(main="conv.cu"):
     h = hashlib.sha256()
-    for f in (main, "fft.cuh", "device_sync.cuh"):
+    for f in (main, "fft.cuh", "device_sync.cuh", "rows.cuh"):
         with open(os.path.join(ROOT, "paper_1911_01353_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -32,13 +32,9 @@
 #include "device_sync.cuh"
 #include "fft.cuh"
 #include "jerk_internal.h"
+#include "rows.cuh"
 
 namespace jerk {
-
-// float swizzle for the staged power row: keeps groups of 4 cells together
-// (16-byte reads of the h = 1 row), at most 2-way conflicts for the
-// digit-reversed writes and 3-way for the h = 2 reads
-__device__ __forceinline__ int swzf(int a) { return a ^ (((a >> 5) & 7) << 2); }
 
 template <int LOG2L>
 struct ConvCfg {
@@ -74,35 +70,6 @@ template <bool ROWS>
 __device__ __forceinline__ int bank_row(const ConvArgs &a, int k) {
     if constexpr (ROWS) return __ldg(a.rows + k);
     return k;
-}
-
-// Store the staged power row of one template into its harmonic-row slots
-// (its n entries): cells q = h p of this segment, p within the row.
-__device__ __forceinline__ void store_rows(const ConvArgs &a, const RowEntries &en, int n, const float *pw,
-                                           const int (*sb)[2], int s0, int j, int NT) {
-    for (int e = 0; e < n; ++e) {
-        const int h = en.h[e];
-        const int64_t off = en.off[e];
-        float *dst = a.slots + off;
-        const int len = (int)en.len[e];
-        const int pf = sb[h - 1][0];
-        const int pl = min(sb[h - 1][1], len - 1);
-        if (pl < pf) continue;                                // this segment is past the row's end
-        if (h == 1) {
-            // p = seg0 + v: whole groups of 4 (seg0 and V are multiples of 4 and
-            // the row is 128-byte aligned), then the ragged end one by one
-            const int n4 = (pl - pf + 1) >> 2;
-            for (int g = j; g < n4; g += NT)
-                if (JERK_CHECK(off + pf + 4 * g + 3 < a.slot_cap, a.chk, kChkRowStore))
-                    *reinterpret_cast<float4 *>(dst + pf + 4 * g) =
-                        *reinterpret_cast<const float4 *>(pw + swzf(4 * g));
-            for (int p = pf + 4 * n4 + j; p <= pl; p += NT)
-                if (JERK_CHECK(off + p < a.slot_cap, a.chk, kChkRowStore)) dst[p] = pw[swzf(p - s0)];
-        } else {
-            for (int p = pf + j; p <= pl; p += NT)
-                if (JERK_CHECK(off + p < a.slot_cap, a.chk, kChkRowStore)) dst[p] = pw[swzf(h * p - s0)];
-        }
-    }
 }
 
 template <int LOG2L, int MODE, bool STATS, bool ROWS>
@@ -317,7 +284,8 @@ conv_kernel(ConvArgs a) {
                 // the previous template's staged row
                 const TplMeta mp = tq[half][(k - 1) & 3];
                 if (mp.e0 < mp.e1)
-                    store_rows(a, rent[half][(k - 1) & 1], mp.e1 - mp.e0, stage, sbound[half], (int)seg0, j, NT);
+                    store_rows(a, rent[half][(k - 1) & 1], mp.e1 - mp.e0, stage, sbound[half], (int)seg0, j, NT,
+                               kChkRowStore);
             }
         fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
@@ -391,7 +359,8 @@ conv_kernel(ConvArgs a) {
         if (!failed && te > tb) {
             const TplMeta mp = tq[half][(te - 1) & 3];
             if (mp.e0 < mp.e1)
-                store_rows(a, rent[half][(te - 1) & 1], mp.e1 - mp.e0, stage, sbound[half], (int)seg0, j, NT);
+                store_rows(a, rent[half][(te - 1) & 1], mp.e1 - mp.e0, stage, sbound[half], (int)seg0, j, NT,
+                           kChkRowStore);
         }
     }
     __syncthreads();

@@ -83,29 +83,37 @@ __device__ __forceinline__ uint32_t idesc() {
     return (1u << 4) | (t << 7) | (t << 10) | ((A_MN ? 1u : 0u) << 15) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// One K = 16 step s (0..7) of D[128 x 128] (tensor memory) = A[128 x 128]
-// B[128 x 128], issued by one elected lane of the calling warp: the whole warp
+// D[128 x 128] (tensor memory) = A[128 x 128] B[128 x 128] as eight K = 16
+// steps, issued by one elected lane of the calling warp: the whole warp
 // executes it, so no lane diverges around the issue.  `ad` and `bd` are the
-// step-0 descriptors; step s starts 2 LBO bytes further along K, 16 in the
-// descriptor's 16-byte address field (which cannot carry: shared addresses
-// are below 2^18).
-template <int PREC, bool A_MN>
-__device__ __forceinline__ void mma_step_warp(uint32_t d_tmem, uint64_t ad, uint64_t bd, int s) {
-    const uint64_t step = (uint64_t)(s * (2 * LBO >> 4));
-    asm volatile(
-        "{\n\t.reg .pred e, p;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(ad + step), "l"(bd + step), "r"(idesc<PREC, A_MN>()), "r"((uint32_t)(s > 0))
-        : "memory");
-}
-
-// all eight steps
+// step-0 shared-memory descriptors; step s starts 2 LBO bytes further along K,
+// 16 more in the descriptors' 16-byte address field (which cannot carry:
+// shared addresses are below 2^18).
+static_assert((2 * LBO >> 4) == 16, "K-step increment of the descriptor address field");
 template <int PREC, bool A_MN>
 __device__ __forceinline__ void mma_tile_warp(uint32_t d_tmem, uint64_t ad, uint64_t bd) {
-#pragma unroll
-    for (int s = 0; s < 8; ++s) mma_step_warp<PREC, A_MN>(d_tmem, ad, bd, s);
+    asm volatile(
+        "{\n\t.reg .pred e, f, t;\n\t.reg .b64 a, b;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 f, 0, 0;\n\t"
+        "setp.eq.b32 t, 0, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, f;\n\t"
+        "add.s64 a, %1, 16;\n\tadd.s64 b, %2, 16;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, 32;\n\tadd.s64 b, %2, 32;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, 48;\n\tadd.s64 b, %2, 48;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, 64;\n\tadd.s64 b, %2, 64;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, 80;\n\tadd.s64 b, %2, 80;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, 96;\n\tadd.s64 b, %2, 96;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t"
+        "add.s64 a, %1, 112;\n\tadd.s64 b, %2, 112;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], a, b, %3, t;\n\t}" ::"r"(d_tmem),
+        "l"(ad), "l"(bd), "r"(idesc<PREC, A_MN>())
+        : "memory");
 }
 
 // the elected lane's products so far arrive on `bar` when they complete
@@ -118,28 +126,48 @@ __device__ __forceinline__ void mma_commit_warp(uint64_t *bar) {
         : "memory");
 }
 
+// st.shared.u16 under a predicate, with no branch around it
+__device__ __forceinline__ void st_shared_u16_if(bool pred, uint32_t addr, uint16_t v) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.shared.u16 [%1], %2;\n\t}" ::"r"((uint32_t)pred),
+        "r"(addr), "h"(v)
+        : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// 16 consecutive FP32 columns of this thread's tensor-memory lane; the wait
-// carries the registers so that no use is scheduled before it
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&x)[16]) {
-    uint32_t r[16];
+// 2 x 16 consecutive FP32 columns of this thread's tensor-memory lane (at
+// taddr0 and taddr1), both loads in flight before one wait; the wait carries
+// the registers so that no use is scheduled before it
+__device__ __forceinline__ void tmem_ld16x2(uint32_t taddr0, uint32_t taddr1, float (&x)[16], float (&y)[16]) {
+    uint32_t r[16], q[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+        : "r"(taddr0));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+          "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+        : "r"(taddr1));
     asm volatile("tcgen05.wait::ld.sync.aligned;"
                  : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
                    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15])
+                   "+r"(r[15]), "+r"(q[0]), "+r"(q[1]), "+r"(q[2]), "+r"(q[3]), "+r"(q[4]), "+r"(q[5]), "+r"(q[6]),
+                   "+r"(q[7]), "+r"(q[8]), "+r"(q[9]), "+r"(q[10]), "+r"(q[11]), "+r"(q[12]), "+r"(q[13]),
+                   "+r"(q[14]), "+r"(q[15])
                  :
                  : "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) x[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) {
+        x[i] = __uint_as_float(r[i]);
+        y[i] = __uint_as_float(q[i]);
+    }
 }
 
 template <bool ROWS>
@@ -317,19 +345,15 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     const uint32_t a1_r1 = a1_r0 + 8 * SBO;
     const uint32_t a3_col = smem_u32(sm + OFF_A3) + (r >> 3) * LBO + (r & 7) * 16 + (8 * seg + 2 * gcol) * SBO;
     const float2 *twt = reinterpret_cast<const float2 *>(sm + OFF_TW) + 16 * 64 * gcol + r;
-    uint16_t *amx_t = amx_s + seg * L + 64 * 16 * gcol + r;   // this thread's cells, stride 64
+    const uint32_t amx_t = smem_u32(amx_s + seg * L + 64 * 16 * gcol + r);   // this thread's cells, stride 128 B
 
     // ---- the three thread phases of one template --------------------------------
-    // Warp 0 issues the products (one elected lane, so the warp never diverges
-    // around an issue) and interleaves their eight K steps with its own share
-    // of a phase: tcgen05.mma blocks while the tensor core's queue is full, so
-    // one step per slice of work keeps the warp from stalling for a whole
-    // product.
+    // Warp 0 issues each product (one elected lane, so the warp never diverges
+    // around an issue) right after the barrier that completes its operand.
     const uint64_t dA1 = sdesc(smem_u32(sm + OFF_A1)), dA3 = sdesc(smem_u32(sm + OFF_A3)),
                    dB = sdesc(smem_u32(sm + OFF_B));
-    // A: Z = X C (scaled) -> A1 (K-major), from ring buffer `b`; issues step 3
-    // of the previous template when `issue3` (warp-uniform)
-    auto phase_a = [&](int b, bool issue3) {
+    // A: Z = X C (scaled) -> A1 (K-major), from ring buffer `b`
+    auto phase_a = [&](int b) {
         const float2 *C = ring + b * L + ka + 64 * 8 * blk;
         uint32_t pr[8], pi[8];                                // [seg 0: 0..3 | seg 1: 4..7]
 #pragma unroll
@@ -341,12 +365,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 pr[4 * s2 + (i >> 1)] = pack2<PREC>(z0.x, z1.x);
                 pi[4 * s2 + (i >> 1)] = pack2<PREC>(z0.y, z1.y);
             }
-            if (issue3) {
-                mma_step_warp<PREC, true>(tmem + 128, dA3, dB, i);
-                mma_step_warp<PREC, true>(tmem + 128, dA3, dB, i + 1);
-            }
         }
-        if (issue3) mma_commit_warp(&mbar3);
         sts128(a1_r0, pr, 0);
         sts128(a1_r0 + 8 * LBO, pi, 0);
         sts128(a1_r1, pr, 4);
@@ -355,8 +374,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     // C: D1 -> twiddle -> A3 (MN-major)
     auto phase_c = [&]() {
         float ur[16], ui[16];
-        tmem_ld16(tmem + tlane + 16 * gcol, ur);
-        tmem_ld16(tmem + tlane + 64 + 16 * gcol, ui);
+        tmem_ld16x2(tmem + tlane + 16 * gcol, tmem + tlane + 64 + 16 * gcol, ur, ui);
         uint32_t pr[8], pi[8];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
@@ -371,14 +389,15 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         sts128(a3_col + 8 * LBO + SBO, pi, 4);
     };
     // E: D3 -> power, running max, statistics, harmonic rows (search) or plane
-    // rows; issues step 1 of the next template when `issue1` (warp-uniform).
+    // rows.
     // The running max and the statistics use |y|^2 before the segment's power
     // scale psc (a monotone factor), applied when they leave the CTA.  The max
-    // runs over all 16 cells: those past nvalid are never read back.
-    auto phase_e = [&](int k, int it, bool issue1) {
+    // runs over all 16 cells: those past nvalid are never read back.  A warp
+    // whose wait expired (`skip`) does none of it.
+    auto phase_e = [&](int k, int it, bool skip) {
+        if (skip) return;
         float yr[16], yi[16];
-        tmem_ld16(tmem + tlane + 128 + 16 * gcol, yr);
-        tmem_ld16(tmem + tlane + 192 + 16 * gcol, yi);
+        tmem_ld16x2(tmem + tlane + 128 + 16 * gcol, tmem + tlane + 192 + 16 * gcol, yr, yi);
         float P[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) P[i] = fmaf(yr[i], yr[i], yi[i] * yi[i]);
@@ -386,32 +405,29 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         if constexpr (MODE == 0) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                if (P[i] > mx[i]) {
-                    mx[i] = P[i];
-                    amx_t[64 * i] = (uint16_t)it;             // rare after the first templates
-                }
-                if (issue1 && (i & 1)) mma_step_warp<PREC, false>(tmem, dA1, dB, i >> 1);
+                st_shared_u16_if(P[i] > mx[i], amx_t + 128 * i, (uint16_t)it);   // rare after the first templates
+                mx[i] = fmaxf(mx[i], P[i]);
             }
-            if (issue1) mma_commit_warp(&mbar1);
             if constexpr (STATS) {
-                float s1 = 0.f, s2 = 0.f;
+                // four independent chains over the thread's cells; cells outside
+                // the segment's valid range count as 0
+                float a4[4] = {0.f, 0.f, 0.f, 0.f}, q4[4] = {0.f, 0.f, 0.f, 0.f};
                 if (nvalid == 16) {
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
-                        s1 += P[i];
-                        s2 = fmaf(P[i], P[i], s2);
+                        a4[i & 3] += P[i];
+                        q4[i & 3] = fmaf(P[i], P[i], q4[i & 3]);
                     }
                 } else {
-                    // cells outside the segment's valid range count as 0
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float pm = i < nvalid ? P[i] : 0.f;
-                        s1 += pm;
-                        s2 = fmaf(pm, pm, s2);
+                        a4[i & 3] += pm;
+                        q4[i & 3] = fmaf(pm, pm, q4[i & 3]);
                     }
                 }
-                c1 += s1;
-                c2 += s2;
+                c1 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
+                c2 += (q4[0] + q4[1]) + (q4[2] + q4[3]);
                 if ((it & 31) == 31) {
                     dacc[0][tid] += (double)c1 * (double)psc;
                     dacc[1][tid] += (double)c2 * ((double)psc * (double)psc);
@@ -419,7 +435,8 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 }
             }
             // harmonic rows: cell q = q0 + 64 i (q0 = seg0 + 1024 gcol + r) is
-            // harmonic h of fundamental cell q / h when h | q
+            // harmonic h of fundamental cell q / h when h | q; stored straight
+            // from registers (lanes hold consecutive cells)
             const RowEntries &en = rent[k & 1];
             const int ne = tq[k & 3].e1 - tq[k & 3].e0;
             const int q0 = seg0 + 1024 * gcol + r;
@@ -427,21 +444,23 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 const int h = en.h[e];
                 float *dst = a.slots + en.off[e];
                 const int len = (int)en.len[e];
-                int quo = q0 / h, rem = q0 - quo * h;
-                if ((64 % h) == 0) {
-                    // h divides 64 (h = 1, 2, 4, 8): all of this thread's cells
-                    // are harmonics of this h, or none is; cell i goes to row
-                    // position quo + i dq while that is below len
-                    if (rem == 0) {
-                        const int dq = 64 / h;
-                        const int iend = quo >= len ? 0 : min(nvalid, (len - quo + dq - 1) / dq);
+                if ((h & (h - 1)) == 0) {
+                    // h = 1, 2, 4, 8 divides 64: all of this thread's cells are
+                    // harmonics of this h, or none is; cell i goes to row
+                    // position quo + i dq (dq = 64 / h) while that is below len
+                    const int lh = __ffs(h) - 1, ldq = 6 - lh;
+                    if ((q0 & (h - 1)) == 0) {
+                        const int quo = q0 >> lh;
+                        const int iend = quo >= len ? 0 : min(nvalid, (len - quo + (1 << ldq) - 1) >> ldq);
+                        float *d = dst + quo;
 #pragma unroll
                         for (int i = 0; i < 16; ++i)
-                            if (i < iend && JERK_CHECK(en.off[e] + quo + i * dq < a.slot_cap, a.chk, kChkTcRowStore))
-                                dst[quo + i * dq] = P[i] * psc;
+                            if (i < iend && JERK_CHECK(en.off[e] + quo + (i << ldq) < a.slot_cap, a.chk, kChkTcRowStore))
+                                d[i << ldq] = P[i] * psc;
                     }
                 } else {
-                    // quotient and remainder stepped by 64 per cell
+                    // h = 3, 5, 6, 7: quotient and remainder stepped by 64 per cell
+                    int quo = q0 / h, rem = q0 - quo * h;
                     const int dq = 64 / h, dr = 64 - dq * h;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
@@ -458,10 +477,6 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 }
             }
         } else {
-            if (issue1) {
-                mma_tile_warp<PREC, false>(tmem, dA1, dB);
-                mma_commit_warp(&mbar1);
-            }
             if (t >= a.t0 && t < a.t0 + a.nt) {
                 const int64_t row0 = (int64_t)(t - a.t0) * bN + seg0;
                 float *prow = a.plane + row0;
@@ -483,7 +498,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     if (nt > 0) {
         if (!fail) fail = !mbar_wait_bounded(&full[0], 0);
         fail = __any_sync(0xffffffffu, fail);
-        if (!fail) phase_a(0, false);
+        if (!fail) phase_a(0);
         fence_async_smem();
         fail = __syncthreads_or(fail);
         if (!fail && warp == 0) {
@@ -497,9 +512,12 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                       &full[0]);
         }
     }
-    for (int it = 0; !fail && it < nt; ++it) {
+    // `fail` is warp-uniform after each wait and CTA-uniform after each
+    // __syncthreads_or; the loop is left only there, so every warp takes the
+    // same barriers.
+    for (int it = 0; it < nt; ++it) {
         // C(it): step 1 of template it has landed in D1
-        fail = !mbar_wait_bounded(&mbar1, (uint32_t)it & 1u);
+        if (!fail) fail = !mbar_wait_bounded(&mbar1, (uint32_t)it & 1u);
         fail = __any_sync(0xffffffffu, fail);
         tc_fence_after();
         if (!fail) phase_c();
@@ -536,14 +554,19 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             }
             cp_async_commit();
         }
+        if (warp == 0) {
+            // step 3 of template it (its operand A3 is complete)
+            tc_fence_after();
+            mma_tile_warp<PREC, true>(tmem + 128, dA3, dB);
+            mma_commit_warp(&mbar3);
+        }
         const bool more = it + 1 < nt;
         if (more) {
             // A(it + 1) while step 3 of template it runs
             const int b = (it + 1) & 1;
-            if (warp == 0) tc_fence_after();
             fail = !mbar_wait_bounded(&full[b], (uint32_t)((it + 1) >> 1) & 1u);
             fail = __any_sync(0xffffffffu, fail);
-            if (!fail) phase_a(b, warp == 0);
+            if (!fail) phase_a(b);
             fence_async_smem();
             if (__syncthreads_or(fail)) {
                 fail = true;
@@ -554,17 +577,18 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 bulk_load(ring + b * L, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + it + 3) * L,
                           (uint32_t)(L * sizeof(float2)), &full[b]);
             }
-            if (warp == 0) tc_fence_after();
-        } else if (warp == 0) {
-            tc_fence_after();
-            mma_tile_warp<PREC, true>(tmem + 128, dA3, dB);
-            mma_commit_warp(&mbar3);
+            if (warp == 0) {
+                // step 1 of template it + 1 (queued behind step 3 of it)
+                tc_fence_after();
+                mma_tile_warp<PREC, false>(tmem, dA1, dB);
+                mma_commit_warp(&mbar1);
+            }
         }
         // E(it): step 3 of template it has landed in D3; step 1 of it + 1 runs meanwhile
         fail = !mbar_wait_bounded(&mbar3, (uint32_t)it & 1u);
         fail = __any_sync(0xffffffffu, fail);
         tc_fence_after();
-        if (!fail) phase_e(tb + it, it, more && warp == 0);
+        phase_e(tb + it, it, fail);
         tc_fence_before();
     }
     if (warp == 2) cp_async_wait_all();                       // no copy in flight past the loop
