@@ -134,6 +134,14 @@ __device__ __forceinline__ void st_shared_u16_if(bool pred, uint32_t addr, uint1
         : "memory");
 }
 
+// acc0 += x0, acc1 += x1 in FP64.  A call, not inlined, so that it stays
+// behind its branch (taken once in 32 templates): predicated in place, the
+// slow FP64 conversions and adds would occupy the FP64 pipe every template.
+__device__ __noinline__ void add_f64_pair(double *acc0, double *acc1, float x0, float x1) {
+    *acc0 += (double)x0;
+    *acc1 += (double)x1;
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -429,8 +437,8 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 c1 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
                 c2 += (q4[0] + q4[1]) + (q4[2] + q4[3]);
                 if ((it & 31) == 31) {
-                    dacc[0][tid] += (double)c1 * (double)psc;
-                    dacc[1][tid] += (double)c2 * ((double)psc * (double)psc);
+                    // unscaled: the segment's scale is applied once, at the end
+                    add_f64_pair(&dacc[0][tid], &dacc[1][tid], c1, c2);
                     c1 = c2 = 0.f;
                 }
             }
@@ -611,8 +619,8 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             }
         }
         if constexpr (STATS) {
-            double d1 = dacc[0][tid] + (double)c1 * (double)psc;
-            double d2 = dacc[1][tid] + (double)c2 * ((double)psc * (double)psc);
+            double d1 = (dacc[0][tid] + (double)c1) * (double)psc;
+            double d2 = (dacc[1][tid] + (double)c2) * ((double)psc * (double)psc);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 d1 += __shfl_xor_sync(0xffffffffu, d1, o);
