@@ -29,6 +29,8 @@
 // another agent is the mbarrier of the bulk copy; it is bounded (about one
 // second of %globaltimer) and on expiry the CTA records an error flag that
 // the host reports as JERK_ETIMEOUT.
+#include <type_traits>
+
 #include "device_sync.cuh"
 #include "fft.cuh"
 #include "jerk_internal.h"
@@ -210,6 +212,12 @@ conv_kernel(ConvArgs a) {
     // last segment of the CTA to finish reading a buffer refills it with
     // template t + NBUF, so the segments never wait on each other.
     bool failed = false;
+    // The last RD outputs r of every thread (cells rv + NT r >= NT (16 - RD))
+    // lie in the overlap of every segment of this group, so the epilogue
+    // skips them and the compiler drops the butterflies that only they need.
+    // The loop is compiled for RD = 0, 1, 2 and the group's V picks one.
+    auto template_loop = [&](auto rd) {
+    constexpr int RK = 16 - decltype(rd)::value;              // outputs kept
     for (int k = tb; k < te; ++k) {                         // processing index
         const int it = k - tb;
         const int b = it % NBUF;
@@ -290,11 +298,11 @@ conv_kernel(ConvArgs a) {
         fft_rest<LOG2L, +1>(v, work, j, twi, bar_half);
         float P[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) P[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
+        for (int r = 0; r < RK; ++r) P[r] = fmaf(v[r].x, v[r].x, v[r].y * v[r].y);
 
         if constexpr (MODE == 0) {
 #pragma unroll
-            for (int r = 0; r < 16; ++r) {
+            for (int r = 0; r < RK; ++r) {
                 if (P[r] > mx[r]) {
                     mx[r] = P[r];
                     amx[rv + NT * r] = (uint16_t)it;          // rare after the first templates
@@ -305,10 +313,10 @@ conv_kernel(ConvArgs a) {
                 // row is never read back at those cells
                 if (vmask >> 16) {
 #pragma unroll
-                    for (int r = RSAFE; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                    for (int r = RSAFE; r < RK; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
                 } else {
 #pragma unroll
-                    for (int r = 0; r < 16; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
+                    for (int r = 0; r < RK; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
                 }
                 // four independent chains of four cells each, then their sum
                 float a4[4], q4[4];
@@ -318,7 +326,7 @@ conv_kernel(ConvArgs a) {
                     q4[i] = P[i] * P[i];
                 }
 #pragma unroll
-                for (int r = 4; r < 16; ++r) {
+                for (int r = 4; r < RK; ++r) {
                     a4[r & 3] += P[r];
                     q4[r & 3] = fmaf(P[r], P[r], q4[r & 3]);
                 }
@@ -334,7 +342,7 @@ conv_kernel(ConvArgs a) {
             // during the next template's transform (whose barriers order it)
             if (tq[half][k & 3].e0 < tq[half][k & 3].e1) {
 #pragma unroll
-                for (int r = 0; r < 16; ++r) {
+                for (int r = 0; r < RK; ++r) {
                     // NT r only sets bits >= 8, which swzf neither reads nor changes
                     if constexpr (NT % 256 == 0)
                         stage[swzf(rv) + NT * r] = P[r];
@@ -347,10 +355,23 @@ conv_kernel(ConvArgs a) {
             const int64_t row0 = (int64_t)(t - a.t0) * (2 * (int64_t)a.items[0].N) + seg0;
             float *row = a.plane + row0;
 #pragma unroll
-            for (int r = 0; r < 16; ++r)
+            for (int r = 0; r < RK; ++r)
                 if (((vmask >> r) & 1u) && JERK_CHECK(row0 + rv + NT * r < a.plane_len, a.chk, kChkPlaneStore))
                     row[rv + NT * r] = P[r];
         }
+    }
+    };
+    if constexpr (LOG2L <= 12) {
+        // (at L = 8192 the three copies spill)
+        const int rd = MODE == 0 ? 16 - (V + NT - 1) / NT : 0;
+        if (rd >= 2)
+            template_loop(std::integral_constant<int, 2>{});
+        else if (rd == 1)
+            template_loop(std::integral_constant<int, 1>{});
+        else
+            template_loop(std::integral_constant<int, 0>{});
+    } else {
+        template_loop(std::integral_constant<int, 0>{});
     }
 
     cp_async_wait_all();
