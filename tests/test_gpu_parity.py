@@ -247,6 +247,49 @@ def test_search_small_tile_shapes(pkg, small, group_size):
     assert compare_candidates(cands, res, tol) <= 2
 
 
+def _dropped_outputs(op, seg_len, group_size):
+    """Per template group (sorted by half-width, runs of group_size), the
+    number of last-pass outputs r that every thread drops: 16 - ceil(V / NT),
+    V = L - 4 max m (interbinning b = 2), at most 2."""
+    nz = 2 * op.zmax // op.dz + 1
+    nw = 2 * op.wmax // op.dw + 1
+    m = [oracle.halfwidth(-op.zmax + (t % nz) * op.dz, -op.wmax + (t // nz) * op.dw, op.pad_bins)
+         for t in range(nz * nw)]
+    order = sorted(range(nz * nw), key=lambda t: (m[t], t))
+    nt = seg_len // 16
+    out = set()
+    for k0 in range(0, len(order), group_size):
+        V = seg_len - 4 * max(m[t] for t in order[k0:k0 + group_size])
+        out.add(min(2, 16 - -(-V // nt)))
+    return out
+
+
+@pytest.mark.parametrize("seg_len,group_size,drops", [(1024, 16, {1, 2}), (2048, 16, {0, 1}),
+                                                       (4096, 16, {0})])
+def test_search_small_dropped_outputs(pkg, small, seg_len, group_size, drops):
+    """The filter skips the last-pass outputs that lie in every segment's
+    overlap (0, 1 or 2 per thread by template group): search mode at segment
+    lengths and group sizes that give each count, every stage, the SIGMA
+    statistics and the candidates against the oracle."""
+    wl, _, F, _ = small
+    op = oracle_params(wl, mode="sigma", thresh=(13.0, 12.0))
+    assert _dropped_outputs(op, seg_len, group_size) == drops
+    res = oracle.search(F, op)
+    tol = PLANE_TOL * max(float(res.maxproj[H][0].max()) for H in op.stages)
+    p = jerk_params(op, F.size, seg_len=seg_len)
+    p.group_size = group_size
+    with pkg.Plan(p) as plan:
+        assert plan.info.seg_len == seg_len
+        cands = _search(pkg, plan, F)
+        mu, sd, _ = plan.stats()
+        for si, H in enumerate(op.stages):
+            M, t = plan.maxproj(si)
+            compare_maxproj(M, t, res.maxproj[H][0], res.maxproj[H][1], res.sums[H][1], tol)
+            assert abs(mu[si] - res.stats[H][0]) <= 1e-5 * res.stats[H][0]
+            assert abs(sd[si] - res.stats[H][1]) <= 1e-5 * res.stats[H][1]
+    assert compare_candidates(cands, res, tol) <= 2
+
+
 def test_search_small_sigma_mode(pkg, small):
     wl, op0, F, _ = small
     op = oracle_params(wl, mode="sigma", thresh=(13.0, 12.0))
