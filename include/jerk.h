@@ -307,6 +307,20 @@ jerk_status jerk_check_waits(jerk_plan plan, int32_t limit_us, void *stream);
  * be NULL.  The counts cover every search of the plan since its creation. */
 jerk_status jerk_check_counts(jerk_plan plan, int64_t *violations, int32_t *first_site, int32_t *compiled_in);
 
+/* (No counterpart in the paper.)  Test hook of the debug build: make the
+ * filter kernels' own bounded waits expire, with no fault.  From the next
+ * search on, at template position `position` (>= 3) of every CTA's template
+ * group, the kernel leaves out one event that its threads wait for: mode 1
+ * the template copy (both filters: the wait on the copy expires), mode 2 the
+ * completion signal of the tensor-core filter's first product, mode 3 that of
+ * its second product (precision 1 and 2 only).  Each waiting CTA gives up after
+ * about one second, drains its copies in flight, frees its tensor memory and
+ * leaves; jerk_candidates then returns JERK_ETIMEOUT and clears the flag.
+ * Mode 0 turns the hook off.  JERK_EINVAL for a mode outside 0..3 or a
+ * position below 3 (the first templates are copied before the loop);
+ * JERK_ESTATE in the release build, which does not contain the hook. */
+jerk_status jerk_check_inject(jerk_plan plan, int32_t mode, int32_t position);
+
 /* Wait for the last search to finish and copy its candidates to h_out
  * (capacity cap records), sorted by (stage position, p).  *n_out receives
  * the number found.  If it exceeds cap (JERK_EOVERFLOW, first cap records

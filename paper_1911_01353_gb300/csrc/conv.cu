@@ -252,7 +252,7 @@ conv_kernel(ConvArgs a) {
         if (j == NT - 32) __threadfence_block();
         if (j == NT - 32 && atomicAdd(&rel[b], 1) == SEGS - 1) {
             rel[b] = 0;
-            if (k + NBUF < te) {
+            if (k + NBUF < te && !inject_at(a, 1, k + NBUF - tb)) {
                 issued[b] += 1;
                 bulk_load(smem + b * L, a.bank + (int64_t)bank_row<ROWS>(a, k + NBUF) * L, (uint32_t)(L * sizeof(float2)),
                           &full[b]);
@@ -265,7 +265,6 @@ conv_kernel(ConvArgs a) {
         // first barrier.  Issued here, where the pass-0 values are in shared memory.
         {
             // (on warps 1 and 2 -- warp 0 at L = 1024 -- away from the buffer release)
-            const int ne = tq[half][k & 3].e1 - tq[half][k & 3].e0;   // this template's slot entries
             if (j == 32) {
                 if (k + 2 < te) cp_async<4>(&tq[half][(k + 2) & 3].t, a.order + k + 2);
                 if (k + 1 < te) {
@@ -275,6 +274,7 @@ conv_kernel(ConvArgs a) {
                 }
             }
             if constexpr (MODE == 0) {
+                const int ne = tq[half][k & 3].e1 - tq[half][k & 3].e0;   // this template's slot entries
                 constexpr int EW = NT >= 128 ? 64 : 0;        // first thread of the entry copies
                 const int i = j - EW;
                 if (i >= 0 && i < ne) {

@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             // step 3 of template it (its operand A3 is complete)
             tc_fence_after();
             mma_tile_warp<PREC, true>(tmem + 128, dA3, dB);
-            mma_commit_warp(&mbar3);
+            if (!inject_at(a, 3, it)) mma_commit_warp(&mbar3);
         }
         const bool more = it + 1 < nt;
         if (more) {
@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 fail = true;
                 break;
             }
-            if (tid == 32 && it + 3 < nt) {                   // buffer b is read: template it + 3 next
+            if (tid == 32 && it + 3 < nt && !inject_at(a, 1, it + 3)) {   // buffer b is read: template it + 3 next
                 issued[b] += 1;
                 bulk_load(ring + b * L, a.bank + (int64_t)tc_bank_row<ROWS>(a, tb + it + 3) * L,
                           (uint32_t)(L * sizeof(float2)), &full[b]);
@@ -589,7 +589,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 // step 1 of template it + 1 (queued behind step 3 of it)
                 tc_fence_after();
                 mma_tile_warp<PREC, false>(tmem, dA1, dB);
-                mma_commit_warp(&mbar1);
+                if (!inject_at(a, 2, it + 1)) mma_commit_warp(&mbar1);
             }
         }
         // E(it): step 3 of template it has landed in D3; step 1 of it + 1 runs meanwhile

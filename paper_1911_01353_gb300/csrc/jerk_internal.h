@@ -67,6 +67,11 @@ struct ConvArgs {
     int *err;                // set to 1 when a bounded device wait expires
     int64_t slot_cap;        // floats of `slots` (bounds checks of the debug build)
     long long *chk;          // violation counter and first site (bounds checks of the debug build)
+    // test hook of the debug build (jerk_check_inject): at template position
+    // inject_pos of every CTA's group, 1 skips the template copy, 2 skips the
+    // completion signal of the tensor-core step 1, 3 that of step 3, so that a
+    // bounded wait expires; 0 (and the release build) does nothing
+    int32_t inject, inject_pos;
     // plane mode
     float *plane;            // [nt][bN]
     int64_t plane_len;       // floats of `plane` (bounds checks of the debug build)
@@ -74,6 +79,17 @@ struct ConvArgs {
     const void *tc_const;    // 16-bit B operand (32 KB) then the twiddle table (float2 [64][64])
     const float *tc_cmax;    // max over the bank of max(|Re C|, |Im C|)
 };
+
+// The test hook: true when the debug build is asked to leave out event `mode`
+// at template position `pos` of the CTA's group (always false in the release
+// build, where the hook is compiled out).
+#ifdef JERK_CHECKS
+__device__ __forceinline__ bool inject_at(const ConvArgs &a, int mode, int pos) {
+    return a.inject == mode && a.inject_pos == pos;
+}
+#else
+__device__ __forceinline__ bool inject_at(const ConvArgs &, int, int) { return false; }
+#endif
 
 // Sites of the debug build's bounds checks (the first failing one is recorded).
 enum CheckSite {
@@ -255,6 +271,7 @@ struct jerk_plan_s {
     unsigned long long *d_count = nullptr;
     int *d_err = nullptr;              // device error flag (bounded waits)
     long long *d_chk = nullptr;        // bounds-check violations and first site (debug build)
+    int32_t inject = 0, inject_pos = 0;   // test hook of the debug build (jerk_check_inject)
     double2 *d_gl = nullptr;
     int n_gl = 0;
     int64_t bytes = 0;

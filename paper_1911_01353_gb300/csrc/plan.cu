@@ -640,6 +640,8 @@ jerk_status enqueue_search(jerk_plan_s *pl, const float2 *const *in, cudaStream_
     a.stat_part = pl->d_stat_part;
     a.err = pl->d_err;
     a.chk = pl->d_chk;
+    a.inject = pl->inject;
+    a.inject_pos = pl->inject_pos;
     a.slot_cap = pl->slot_cap;
     a.tc_const = pl->d_tc;
     a.tc_cmax = pl->d_cmax;
@@ -1160,6 +1162,8 @@ jerk_status jerk_plane(jerk_plan pl, const void *d_spec, int64_t n, int32_t t0, 
     a.plane = d_out;
     a.err = pl->d_err;
     a.chk = pl->d_chk;
+    a.inject = pl->inject;
+    a.inject_pos = pl->inject_pos;
     a.plane_len = (int64_t)nt * 2 * n;
     a.slot_beg = pl->d_slot_beg;
     a.tc_const = pl->d_tc;
@@ -1436,6 +1440,17 @@ jerk_status jerk_check_waits(jerk_plan pl, int32_t limit_us, void *stream) {
     JCHECK(cudaEventRecord(pl->done, st));
     JCHECK(cudaEventSynchronize(pl->done));
     return device_error(pl);          // JERK_ETIMEOUT, and the flag is cleared for the next search
+}
+
+jerk_status jerk_check_inject(jerk_plan pl, int32_t mode, int32_t position) {
+    if (!pl || mode < 0 || mode > 3 || (mode > 0 && position < 3)) return JERK_EINVAL;
+#ifdef JERK_CHECKS
+    pl->inject = mode;
+    pl->inject_pos = mode ? position : 0;
+    return JERK_OK;
+#else
+    return JERK_ESTATE;
+#endif
 }
 
 jerk_status jerk_check_counts(jerk_plan pl, int64_t *violations, int32_t *first_site, int32_t *compiled_in) {

@@ -27,7 +27,7 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
            "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits",
-           "jerk_measure_peaks", "jerk_check_counts", "jerk_params_validate", "jerk_search_range",
+           "jerk_measure_peaks", "jerk_check_counts", "jerk_check_inject", "jerk_params_validate", "jerk_search_range",
            "jerk_range_sums", "jerk_select", "jerk_subharmonic")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
             "jerk_refine": ([vp, vp, i64, ctypes.POINTER(Candidate), i32, ctypes.POINTER(ctypes.c_double),
                              ctypes.POINTER(i32), ctypes.POINTER(Refined), vp], st),
             "jerk_check_counts": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)], st),
+            "jerk_check_inject": ([vp, i32, i32], st),
             "jerk_check_waits": ([vp, i32, vp], st),
             "jerk_measure_peaks": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                    st),
@@ -403,6 +404,14 @@ class Plan:
         _check(lib().jerk_check_counts(self._h, ctypes.byref(v), ctypes.byref(site), ctypes.byref(on)),
                "jerk_check_counts")
         return int(v.value), int(site.value), bool(on.value)
+
+    def check_inject(self, mode: int, position: int = 3):
+        """Set the debug build's test hook (jerk_check_inject); returns the
+        status code (JERK_ESTATE from the release build)."""
+        code = lib().jerk_check_inject(self._h, int(mode), int(position))
+        if code == JERK_EINVAL:
+            _check(code, "jerk_check_inject")
+        return code
 
     def stats(self, item: int = 0):
         k = int(self.params.n_stages)
