@@ -13,10 +13,19 @@
 
 namespace jerk {
 
-// float swizzle for the staged power row: keeps groups of 4 cells together
-// (16-byte reads of the h = 1 row), at most 2-way conflicts for the
-// digit-reversed writes of the FP32 filter and 3-way for the h = 2 reads
-__device__ __forceinline__ int swzf(int a) { return a ^ (((a >> 5) & 7) << 2); }
+// float swizzle for the staged power row: bits 5-7 of the cell flipped into
+// bits 1-3.  The FP32 filter's digit-reversed writes (lanes differ in cell
+// bits 0 and 4-7) then meet 32 distinct banks, the h = 2 reads at most 3.  A
+// group of 4 cells stays in one 16-byte block, its two pairs swapped when
+// bit 5 of the cell is set (row4 undoes it).
+__device__ __forceinline__ int swzf(int a) { return a ^ (((a >> 5) & 7) << 1); }
+
+// cells 4g .. 4g + 3 of the staged row, in order, from one 16-byte load
+__device__ __forceinline__ float4 row4(const float *pw, int g) {
+    const int a = 4 * g;
+    const float4 v = *reinterpret_cast<const float4 *>(pw + (swzf(a) & ~3));
+    return ((a >> 5) & 1) ? make_float4(v.z, v.w, v.x, v.y) : v;
+}
 
 // Store the staged power row `pw` of one template (cell c of the segment at
 // pw[swzf(c)], the segment starting at cell s0) into its n row entries, with
@@ -40,8 +49,7 @@ __device__ __forceinline__ void store_rows(const ConvArgs &a, const RowEntries &
             const int n4 = (pl - pf + 1) >> 2;
             for (int g = j; g < n4; g += nt)
                 if (JERK_CHECK(off + pf + 4 * g + 3 < a.slot_cap, a.chk, site))
-                    *reinterpret_cast<float4 *>(dst + pf + 4 * g) =
-                        *reinterpret_cast<const float4 *>(pw + swzf(4 * g));
+                    *reinterpret_cast<float4 *>(dst + pf + 4 * g) = row4(pw, g);
             for (int p = pf + 4 * n4 + j; p <= pl; p += nt)
                 if (JERK_CHECK(off + p < a.slot_cap, a.chk, site)) dst[p] = pw[swzf(p - s0)];
         } else {
