@@ -318,20 +318,27 @@ conv_kernel(ConvArgs a) {
 #pragma unroll
                     for (int r = 0; r < RK; ++r) P[r] = (vmask >> r) & 1u ? P[r] : 0.f;
                 }
-                // four independent chains of four cells each, then their sum
-                float a4[4], q4[4];
+                // four independent chains (two packed pairs of cells), then their sum
+                float2 a2[2], q2[2];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    a4[i] = P[i];
-                    q4[i] = P[i] * P[i];
+                for (int i = 0; i < 2; ++i) {
+                    const float2 p = make_float2(P[2 * i], P[2 * i + 1]);
+                    a2[i] = p;
+                    q2[i] = fma2(p, p, make_float2(0.f, 0.f));
                 }
 #pragma unroll
-                for (int r = 4; r < RK; ++r) {
-                    a4[r & 3] += P[r];
-                    q4[r & 3] = fmaf(P[r], P[r], q4[r & 3]);
+                for (int r = 4; r + 1 < RK; r += 2) {
+                    const float2 p = make_float2(P[r], P[r + 1]);
+                    a2[(r >> 1) & 1] = add2(a2[(r >> 1) & 1], p);
+                    q2[(r >> 1) & 1] = fma2(p, p, q2[(r >> 1) & 1]);
                 }
-                fa0 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
-                fa1 += (q4[0] + q4[1]) + (q4[2] + q4[3]);
+                if constexpr (RK & 1) {
+                    a2[0].x += P[RK - 1];
+                    q2[0].x = fmaf(P[RK - 1], P[RK - 1], q2[0].x);
+                }
+                const float2 as = add2(a2[0], a2[1]), qs = add2(q2[0], q2[1]);
+                fa0 += as.x + as.y;
+                fa1 += qs.x + qs.y;
                 if ((it & 31) == 31) {
                     dacc[0][tid] += (double)fa0;
                     dacc[1][tid] += (double)fa1;

@@ -18,10 +18,65 @@
 
 namespace jerk {
 
-__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Packed FP32 (add/sub/fma .f32x2, sm_100 and later) on the (re, im) pair of
+// a complex value: one instruction where the scalar form takes two, with
+// the same round-to-nearest result in each lane.  The packed forms run at the
+// scalar FP32 rate but free an issue slot for the kernels' other
+// instructions.  Host code (and device passes for older architectures, in
+// host-side tests) takes the plain lane-by-lane form.
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+#define JERK_PACKED_F32 1
+#else
+#define JERK_PACKED_F32 0
+#endif
+
+__host__ __device__ __forceinline__ float2 add2(float2 a, float2 b) {
+#if JERK_PACKED_F32
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+#if JERK_PACKED_F32
+    float2 d;
+    asm("{.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+// a * b + c, lane by lane
+__host__ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+#if JERK_PACKED_F32
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+// a * (k, k) + c
+__host__ __device__ __forceinline__ float2 fma2k(float k, float2 a, float2 c) { return fma2(make_float2(k, k), a, c); }
+
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return add2(a, b); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return sub2(a, b); }
 __host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a + SIGN i b and a - SIGN i b: the rotation swaps b's parts, so each lane
+// takes its own scalar operation (no packed form without a register swap)
+template <int SIGN>
+__host__ __device__ __forceinline__ float2 cadd_i(float2 a, float2 b) {
+    return SIGN > 0 ? make_float2(a.x - b.y, a.y + b.x) : make_float2(a.x + b.y, a.y - b.x);
+}
+template <int SIGN>
+__host__ __device__ __forceinline__ float2 csub_i(float2 a, float2 b) {
+    return cadd_i<-SIGN>(a, b);
 }
 
 // Padded shared-memory layout: one spare element after every 16, so that the
@@ -58,12 +113,12 @@ __host__ __device__ __forceinline__ void dft2(float2 &a0, float2 &a1) {
 
 template <int SIGN>
 __host__ __device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3) {
-    float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
-    float2 s13 = cadd(a1, a3), d13 = mul_i<SIGN>(csub(a1, a3));
+    const float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+    const float2 s13 = cadd(a1, a3), e13 = csub(a1, a3);
     a0 = cadd(s02, s13);
     a2 = csub(s02, s13);
-    a1 = cadd(d02, d13);
-    a3 = csub(d02, d13);
+    a1 = cadd_i<SIGN>(d02, e13);
+    a3 = csub_i<SIGN>(d02, e13);
 }
 
 // exp(SIGN 2 pi i m / 16) as constants
@@ -83,8 +138,10 @@ __host__ __device__ __forceinline__ float2 w16() {
 // The twiddles exp(SIGN 2 pi i m / 8) with m odd are c (+-1 +- i), c = 1/sqrt 2:
 // a butterfly x0 +- w b with such a w is formed as x0 +- c (u, v), (u, v) the
 // sums and differences of b's parts (eighth_root_parts), with fused
-// multiply-adds -- six instructions where a complex product and two complex
-// additions take eight.
+// multiply-adds: two scalar additions and two packed fused multiply-adds
+// where a complex product and two complex additions take eight scalar
+// instructions.  Complex additions without a rotation are one packed
+// instruction; those with a +-i rotation (cadd_i) stay two scalar ones.
 constexpr float kRsqrt2 = 0.70710678118654752f;
 
 // (u, v) with w b = c (u, v) for w = exp(SIGN 2 pi i M / 8), M = 1 or 3
@@ -120,38 +177,37 @@ __host__ __device__ __forceinline__ void dft16(float2 (&a)[16]) {
     // r1 = 1: x1 = C1 w^1, x2 = C2 w^2, x3 = C3 w^3
     {
         const float2 q = eighth_root_parts<SIGN, 1>(a[6]);         // w^2 C2 = c q
-        const float2 s02 = make_float2(fmaf(kRsqrt2, q.x, a[4].x), fmaf(kRsqrt2, q.y, a[4].y));
-        const float2 d02 = make_float2(fmaf(-kRsqrt2, q.x, a[4].x), fmaf(-kRsqrt2, q.y, a[4].y));
+        const float2 s02 = fma2k(kRsqrt2, q, a[4]);
+        const float2 d02 = fma2k(-kRsqrt2, q, a[4]);
         const float2 x1 = cmul(a[5], w16<SIGN, 1>()), x3 = cmul(a[7], w16<SIGN, 3>());
-        const float2 s13 = cadd(x1, x3), d13 = mul_i<SIGN>(csub(x1, x3));
+        const float2 s13 = cadd(x1, x3), e13 = csub(x1, x3);
         y[1] = cadd(s02, s13);
         y[9] = csub(s02, s13);
-        y[5] = cadd(d02, d13);
-        y[13] = csub(d02, d13);
+        y[5] = cadd_i<SIGN>(d02, e13);
+        y[13] = csub_i<SIGN>(d02, e13);
     }
     // r1 = 2: x1 = C1 w^2, x2 = C2 w^4 = SIGN i C2, x3 = C3 w^6 = w^2 (SIGN i C3)
     {
-        const float2 i2 = mul_i<SIGN>(a[10]), i3 = mul_i<SIGN>(a[11]);
-        const float2 s02 = cadd(a[8], i2), d02 = csub(a[8], i2);
-        const float2 e = cadd(a[9], i3), f = csub(a[9], i3);       // x1 + x3 = w^2 e, x1 - x3 = w^2 f
+        const float2 s02 = cadd_i<SIGN>(a[8], a[10]), d02 = csub_i<SIGN>(a[8], a[10]);
+        const float2 e = cadd_i<SIGN>(a[9], a[11]), f = csub_i<SIGN>(a[9], a[11]);   // x1 + x3 = w^2 e, x1 - x3 = w^2 f
         const float2 qe = eighth_root_parts<SIGN, 1>(e);            // w^2 e = c qe
-        const float2 qf = mul_i<SIGN>(eighth_root_parts<SIGN, 1>(f));   // SIGN i w^2 f = c qf
-        y[2] = make_float2(fmaf(kRsqrt2, qe.x, s02.x), fmaf(kRsqrt2, qe.y, s02.y));
-        y[10] = make_float2(fmaf(-kRsqrt2, qe.x, s02.x), fmaf(-kRsqrt2, qe.y, s02.y));
-        y[6] = make_float2(fmaf(kRsqrt2, qf.x, d02.x), fmaf(kRsqrt2, qf.y, d02.y));
-        y[14] = make_float2(fmaf(-kRsqrt2, qf.x, d02.x), fmaf(-kRsqrt2, qf.y, d02.y));
+        const float2 qf = mul_i<SIGN>(eighth_root_parts<SIGN, 1>(f));   // SIGN i w^2 f = c qf (parts formed in place)
+        y[2] = fma2k(kRsqrt2, qe, s02);
+        y[10] = fma2k(-kRsqrt2, qe, s02);
+        y[6] = fma2k(kRsqrt2, qf, d02);
+        y[14] = fma2k(-kRsqrt2, qf, d02);
     }
     // r1 = 3: x1 = C1 w^3, x2 = C2 w^6, x3 = C3 w^9
     {
         const float2 q = eighth_root_parts<SIGN, 3>(a[14]);        // w^6 C2 = c q
-        const float2 s02 = make_float2(fmaf(kRsqrt2, q.x, a[12].x), fmaf(kRsqrt2, q.y, a[12].y));
-        const float2 d02 = make_float2(fmaf(-kRsqrt2, q.x, a[12].x), fmaf(-kRsqrt2, q.y, a[12].y));
+        const float2 s02 = fma2k(kRsqrt2, q, a[12]);
+        const float2 d02 = fma2k(-kRsqrt2, q, a[12]);
         const float2 x1 = cmul(a[13], w16<SIGN, 3>()), x3 = cmul(a[15], w16<SIGN, 9>());
-        const float2 s13 = cadd(x1, x3), d13 = mul_i<SIGN>(csub(x1, x3));
+        const float2 s13 = cadd(x1, x3), e13 = csub(x1, x3);
         y[3] = cadd(s02, s13);
         y[11] = csub(s02, s13);
-        y[7] = cadd(d02, d13);
-        y[15] = csub(d02, d13);
+        y[7] = cadd_i<SIGN>(d02, e13);
+        y[15] = csub_i<SIGN>(d02, e13);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) a[i] = y[i];
@@ -168,18 +224,15 @@ __host__ __device__ __forceinline__ void dft8(float2 (&a)[8]) {
     y[4] = csub(a[0], a[1]);
     {
         const float2 q = eighth_root_parts<SIGN, 1>(a[3]);          // w8^1 C1 = c q
-        y[1] = make_float2(fmaf(kRsqrt2, q.x, a[2].x), fmaf(kRsqrt2, q.y, a[2].y));
-        y[5] = make_float2(fmaf(-kRsqrt2, q.x, a[2].x), fmaf(-kRsqrt2, q.y, a[2].y));
+        y[1] = fma2k(kRsqrt2, q, a[2]);
+        y[5] = fma2k(-kRsqrt2, q, a[2]);
     }
-    {
-        const float2 t = mul_i<SIGN>(a[5]);                          // w8^2 = SIGN i
-        y[2] = cadd(a[4], t);
-        y[6] = csub(a[4], t);
-    }
+    y[2] = cadd_i<SIGN>(a[4], a[5]);                                  // w8^2 = SIGN i
+    y[6] = csub_i<SIGN>(a[4], a[5]);
     {
         const float2 q = eighth_root_parts<SIGN, 3>(a[7]);          // w8^3 C1 = c q
-        y[3] = make_float2(fmaf(kRsqrt2, q.x, a[6].x), fmaf(kRsqrt2, q.y, a[6].y));
-        y[7] = make_float2(fmaf(-kRsqrt2, q.x, a[6].x), fmaf(-kRsqrt2, q.y, a[6].y));
+        y[3] = fma2k(kRsqrt2, q, a[6]);
+        y[7] = fma2k(-kRsqrt2, q, a[6]);
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) a[i] = y[i];
