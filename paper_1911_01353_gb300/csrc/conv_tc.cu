@@ -46,7 +46,7 @@ constexpr int OPB = 128 * 128 * 2;                        // one 16-bit 128 x 12
 constexpr int OFF_A1 = 2 * L * 8;                         // after the two-deep template ring
 constexpr int OFF_A3 = OFF_A1 + OPB;
 constexpr int OFF_B = OFF_A3 + OPB;                       // B, then the twiddle table (one bulk copy)
-constexpr int OFF_TW = OFF_B + OPB;                       // float2 [n2][k1] = w^{k1 n2}
+constexpr int OFF_TW = OFF_B + OPB;                       // w^{k1 n2} for n2 = 2p, 2p + 1: float4 [p][k1] (re, re, im, im)
 constexpr int OFF_AMX = OFF_TW + 64 * 64 * 8;             // uint16 [SEGS][L]: argmax offset in the group
 constexpr int SMEM = OFF_AMX + SEGS * L * 2;              // 212 992 bytes
 constexpr uint32_t TMEM_COLS = 256;                       // D1: columns 0..127, D3: 128..255
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     const uint32_t a1_r0 = smem_u32(sm + OFF_A1) + (ka >> 3) * SBO + (ka & 7) * 16 + blk * LBO;
     const uint32_t a1_r1 = a1_r0 + 8 * SBO;
     const uint32_t a3_col = smem_u32(sm + OFF_A3) + (r >> 3) * LBO + (r & 7) * 16 + (8 * seg + 2 * gcol) * SBO;
-    const float2 *twt = reinterpret_cast<const float2 *>(sm + OFF_TW) + 16 * 64 * gcol + r;
+    const float4 *twt = reinterpret_cast<const float4 *>(sm + OFF_TW) + 8 * 64 * gcol + r;
     const uint32_t amx_t = smem_u32(amx_s + seg * L + 64 * 16 * gcol + r);   // this thread's cells, stride 128 B
 
     // ---- the three thread phases of one template --------------------------------
@@ -386,10 +386,14 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         uint32_t pr[8], pi[8];
 #pragma unroll
         for (int i = 0; i < 16; i += 2) {
-            const float2 u0 = cmul(make_float2(ur[i], ui[i]), twt[i * 64]);
-            const float2 u1 = cmul(make_float2(ur[i + 1], ui[i + 1]), twt[(i + 1) * 64]);
-            pr[i >> 1] = pack2<PREC>(u0.x, u1.x);
-            pi[i >> 1] = pack2<PREC>(u0.y, u1.y);
+            // cells i, i + 1 at once: packed complex product with their twiddles
+            const float4 w = twt[(i >> 1) * 64];
+            const float2 re = make_float2(ur[i], ur[i + 1]), im = make_float2(ui[i], ui[i + 1]);
+            const float2 wr = make_float2(w.x, w.y), wi = make_float2(w.z, w.w);
+            const float2 ore = sub2(mul2(re, wr), mul2(im, wi));
+            const float2 oim = fma2(re, wi, mul2(im, wr));
+            pr[i >> 1] = pack2<PREC>(ore.x, ore.y);
+            pi[i >> 1] = pack2<PREC>(oim.x, oim.y);
         }
         sts128(a3_col, pr, 0);
         sts128(a3_col + SBO, pr, 4);
@@ -408,7 +412,12 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
         tmem_ld16x2(tmem + tlane + 128 + 16 * gcol, tmem + tlane + 192 + 16 * gcol, yr, yi);
         float P[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) P[i] = fmaf(yr[i], yr[i], yi[i] * yi[i]);
+        for (int i = 0; i < 16; i += 2) {
+            const float2 re = make_float2(yr[i], yr[i + 1]), im = make_float2(yi[i], yi[i + 1]);
+            const float2 p2 = fma2(re, re, mul2(im, im));    // two cells per packed instruction
+            P[i] = p2.x;
+            P[i + 1] = p2.y;
+        }
         const int t = tq[k & 3].t;
         if constexpr (MODE == 0) {
 #pragma unroll
@@ -417,25 +426,27 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 mx[i] = fmaxf(mx[i], P[i]);
             }
             if constexpr (STATS) {
-                // four independent chains over the thread's cells; cells outside
-                // the segment's valid range count as 0
-                float a4[4] = {0.f, 0.f, 0.f, 0.f}, q4[4] = {0.f, 0.f, 0.f, 0.f};
+                // four independent chains over the thread's cells (two packed
+                // pairs); cells outside the segment's valid range count as 0
+                float2 a2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, q2[2] = {a2[0], a2[0]};
                 if (nvalid == 16) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        a4[i & 3] += P[i];
-                        q4[i & 3] = fmaf(P[i], P[i], q4[i & 3]);
+                    for (int i = 0; i < 16; i += 2) {
+                        const float2 p = make_float2(P[i], P[i + 1]);
+                        a2[(i >> 1) & 1] = add2(a2[(i >> 1) & 1], p);
+                        q2[(i >> 1) & 1] = fma2(p, p, q2[(i >> 1) & 1]);
                     }
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const float pm = i < nvalid ? P[i] : 0.f;
-                        a4[i & 3] += pm;
-                        q4[i & 3] = fmaf(pm, pm, q4[i & 3]);
+                    for (int i = 0; i < 16; i += 2) {
+                        const float2 p = make_float2(i < nvalid ? P[i] : 0.f, i + 1 < nvalid ? P[i + 1] : 0.f);
+                        a2[(i >> 1) & 1] = add2(a2[(i >> 1) & 1], p);
+                        q2[(i >> 1) & 1] = fma2(p, p, q2[(i >> 1) & 1]);
                     }
                 }
-                c1 += (a4[0] + a4[1]) + (a4[2] + a4[3]);
-                c2 += (q4[0] + q4[1]) + (q4[2] + q4[3]);
+                const float2 as = add2(a2[0], a2[1]), qs = add2(q2[0], q2[1]);
+                c1 += as.x + as.y;
+                c2 += qs.x + qs.y;
                 if ((it & 31) == 31) {
                     // unscaled: the segment's scale is applied once, at the end
                     add_f64_pair(&dacc[0][tid], &dacc[1][tid], c1, c2);

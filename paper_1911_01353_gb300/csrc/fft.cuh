@@ -52,6 +52,13 @@ __host__ __device__ __forceinline__ float2 sub2(float2 a, float2 b) {
     return make_float2(a.x - b.x, a.y - b.y);
 #endif
 }
+__host__ __device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+#if JERK_PACKED_F32
+    return __fmul2_rn(a, b);
+#else
+    return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
 // a * b + c, lane by lane
 __host__ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 #if JERK_PACKED_F32

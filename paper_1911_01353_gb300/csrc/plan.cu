@@ -745,8 +745,10 @@ jerk_status finish_search(jerk_plan_s *pl, cudaStream_t st, int count, bool prof
 //                                               c: re | im of the output index),
 // as a 16-bit (BF16 for precision 1, FP16 for 2) K-major 128 x 128 operand in
 // 8 x 8 core matrices (128 B apart along K, 2048 B along N), followed by the
-// twiddle table tw[n2][k1] = exp(+2 pi i k1 n2 / 4096) as float2.  FP64
-// arithmetic, rounded once.
+// twiddle table tw[n2][k1] = exp(+2 pi i k1 n2 / 4096), stored for two rows
+// n2 = 2p, 2p + 1 at a time as float4 [p][k1] = (Re tw[2p][k1], Re tw[2p+1][k1],
+// Im tw[2p][k1], Im tw[2p+1][k1]) so that one 16-byte load feeds a packed
+// complex product of two cells.  FP64 arithmetic, rounded once.
 std::vector<unsigned char> tc_constants(int precision) {
     const double two_pi = 6.283185307179586476925286766559;
     std::vector<unsigned char> out(128 * 128 * 2 + 64 * 64 * 8, 0);
@@ -773,8 +775,9 @@ std::vector<unsigned char> tc_constants(int precision) {
     for (int n2 = 0; n2 < 64; ++n2)
         for (int k1 = 0; k1 < 64; ++k1) {
             const double ang = two_pi * (double)(k1 * n2) / 4096.0;
-            tw[2 * (n2 * 64 + k1)] = (float)std::cos(ang);
-            tw[2 * (n2 * 64 + k1) + 1] = (float)std::sin(ang);
+            float *e = tw + 4 * ((n2 >> 1) * 64 + k1) + (n2 & 1);
+            e[0] = (float)std::cos(ang);
+            e[2] = (float)std::sin(ang);
         }
     return out;
 }
