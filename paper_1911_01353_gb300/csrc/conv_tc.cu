@@ -271,17 +271,21 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
     // Operand-build mapping: thread (ka, blk) forms Z for k = ka + 64 k2, k2 in
     // [8 blk, 8 blk + 8), of BOTH segments, so each template value is read from
     // shared memory once per CTA.  It keeps X[s][ka + 64 (8 blk + i)], s = 0, 1.
+    // Values i and i + 1 are kept as packed pairs (xr: real parts, xi:
+    // imaginary parts), matching the bank's paired form (f, f + 64).
     const int ka = tid & 63, blk = tid >> 6;
-    float2 xa[SEGS][8];
+    float2 xr[SEGS][4], xi[SEGS][4];
     {
         float m[SEGS] = {0.f, 0.f};
 #pragma unroll
         for (int s2 = 0; s2 < SEGS; ++s2) {
             const float2 *ws = reinterpret_cast<const float2 *>(sm) + s2 * WPAD;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                xa[s2][i] = ws[ka + 64 * (8 * blk + i)];
-                m[s2] = fmaxf(m[s2], fmaxf(fabsf(xa[s2][i].x), fabsf(xa[s2][i].y)));
+            for (int i = 0; i < 8; i += 2) {
+                const float2 x0 = ws[ka + 64 * (8 * blk + i)], x1 = ws[ka + 64 * (8 * blk + i + 1)];
+                xr[s2][i >> 1] = make_float2(x0.x, x1.x);
+                xi[s2][i >> 1] = make_float2(x0.y, x1.y);
+                m[s2] = fmaxf(m[s2], fmaxf(fmaxf(fabsf(x0.x), fabsf(x0.y)), fmaxf(fabsf(x1.x), fabsf(x1.y))));
             }
         }
 #pragma unroll
@@ -325,7 +329,10 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             const float xm = __int_as_float(xmax_bits[s2]);
             const float sc = (xm > 0.f && cm > 0.f) ? 1.0f / (xm * cm) : 1.0f;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) xa[s2][i] = make_float2(xa[s2][i].x * sc, xa[s2][i].y * sc);
+            for (int i = 0; i < 4; ++i) {
+                xr[s2][i] = make_float2(xr[s2][i].x * sc, xr[s2][i].y * sc);
+                xi[s2][i] = make_float2(xi[s2][i].x * sc, xi[s2][i].y * sc);
+            }
             if (s2 == seg) psc = 1.0f / (sc * sc);
         }
     }
@@ -362,16 +369,20 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                    dB = sdesc(smem_u32(sm + OFF_B));
     // A: Z = X C (scaled) -> A1 (K-major), from ring buffer `b`
     auto phase_a = [&](int b) {
-        const float2 *C = ring + b * L + ka + 64 * 8 * blk;
+        // template values f = ka + 64 (8 blk + i) and f + 64, paired in the bank
+        const float4 *C = reinterpret_cast<const float4 *>(ring + b * L) + ka + 64 * 4 * blk;
         uint32_t pr[8], pi[8];                                // [seg 0: 0..3 | seg 1: 4..7]
 #pragma unroll
-        for (int i = 0; i < 8; i += 2) {
-            const float2 c0 = C[64 * i], c1 = C[64 * (i + 1)];
+        for (int i = 0; i < 4; ++i) {
+            const float4 c = C[64 * i];
+            const float2 cr = make_float2(c.x, c.y), ci = make_float2(c.z, c.w);
 #pragma unroll
             for (int s2 = 0; s2 < SEGS; ++s2) {
-                const float2 z0 = cmul(xa[s2][i], c0), z1 = cmul(xa[s2][i + 1], c1);
-                pr[4 * s2 + (i >> 1)] = pack2<PREC>(z0.x, z1.x);
-                pi[4 * s2 + (i >> 1)] = pack2<PREC>(z0.y, z1.y);
+                // two complex products per packed instruction
+                const float2 zr = sub2(mul2(xr[s2][i], cr), mul2(xi[s2][i], ci));
+                const float2 zi = fma2(xr[s2][i], ci, mul2(xi[s2][i], cr));
+                pr[4 * s2 + i] = pack2<PREC>(zr.x, zr.y);
+                pi[4 * s2 + i] = pack2<PREC>(zi.x, zi.y);
             }
         }
         sts128(a1_r0, pr, 0);

@@ -153,6 +153,9 @@ cudaError_t launch_taps(const int32_t *zt, const int32_t *wt, const int32_t *tli
 cudaError_t launch_template_fft(const double2 *taps, const int32_t *shift, const int32_t *klen, int32_t nt, int K,
                                 int L, const double2 *tw, int fold_r0, float2 *bank, cudaStream_t st);
 int conv_fold_radix(int log2L);      // radix of the FP32 filter's first inverse pass (the bank's folded form)
+// the tensor-core filter's bank pairs spectrum values f and f + kTcBankPair
+// (the two rows of a DFT block one thread multiplies together)
+constexpr int kTcBankPair = 64;
 cudaError_t launch_twiddles64(double2 *tw, int L, cudaStream_t st);
 cudaError_t launch_conv(int log2L, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);
 cudaError_t launch_conv_tc(int precision, int mode, bool stats, const ConvArgs &a, int n_ctas, cudaStream_t st);

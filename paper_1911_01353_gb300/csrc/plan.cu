@@ -1112,7 +1112,7 @@ jerk_status jerk_templates(jerk_plan pl, void *stream) {
                         pl->d_gl, pl->n_gl, taps, st);
         if (e == cudaSuccess)
             e = launch_template_fft(taps, d_shift + k0, d_klen + k0, nt, pl->K, pl->L, tw,
-                                    pl->prm.precision ? 0 : conv_fold_radix(pl->log2L),
+                                    pl->prm.precision ? -kTcBankPair : conv_fold_radix(pl->log2L),
                                     pl->d_bank + (size_t)k0 * pl->L, st);
     }
     if (e == cudaSuccess) e = launch_bank_maxabs(pl->d_bank, (int64_t)pl->T * pl->L, pl->d_cmax, pl->sms, st);

@@ -149,6 +149,8 @@ __global__ void twiddle64_kernel(double2 *tw, int L) {
 // both computed in FP64 before the one rounding to FP32 and stored
 // interleaved, row[2 f] = Ge[f], row[2 f + 1] = Go[f], so that one 16-byte
 // shared-memory load gives a thread both factors of its spectrum value X[f].
+// fold_r0 < 0 stores the paired form of the tensor-core filter (below); 0
+// stores G as it is.
 __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int32_t *__restrict__ shift,
                                     const int32_t *__restrict__ klen, int K, int L, int log2L,
                                     const double2 *__restrict__ tw, int fold_r0, float2 *__restrict__ bank) {
@@ -191,6 +193,20 @@ __global__ void template_fft_kernel(const double2 *__restrict__ taps, const int3
             }
             const int slot = f < half ? 2 * f : 2 * (f - half) + 1;
             dst[slot] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+        }
+        return;
+    }
+    if (fold_r0 < 0) {
+        // paired form of the tensor-core filter: spectrum values f and f + P
+        // (P = -fold_r0, bit log2 P of f clear) side by side as (Re f, Re f+P)
+        // (Im f, Im f+P) at float2 slots 2 q and 2 q + 1, q = f with that bit
+        // removed, so that one 16-byte load feeds a packed product of two
+        // values
+        const int P = -fold_r0;
+        for (int q = threadIdx.x; q < L / 2; q += blockDim.x) {
+            const int f = (q & (P - 1)) | ((q & ~(P - 1)) << 1);
+            dst[2 * q] = make_float2((float)(buf[f].x * inv), (float)(buf[f + P].x * inv));
+            dst[2 * q + 1] = make_float2((float)(buf[f].y * inv), (float)(buf[f + P].y * inv));
         }
         return;
     }

@@ -119,11 +119,23 @@ def fold_spectrum(G, L):
     return out
 
 
+def pair_spectrum(G, P):
+    """The paired form the tensor-core filter's bank stores: values f and
+    f + P (bit log2 P of f clear) side by side, real parts then imaginary
+    parts, as two complex64 slots per pair."""
+    f = np.arange(G.size)
+    f = f[(f & P) == 0]
+    out = np.empty(G.size, dtype=complex)
+    out[0::2] = G[f].real + 1j * G[f + P].real
+    out[1::2] = G[f].imag + 1j * G[f + P].imag
+    return out
+
+
 @pytest.mark.parametrize("precision,seg_len", [(0, 0), (0, 2048), (0, 8192), (2, 0)])
 def test_bank_spectra(pkg, precision, seg_len):
     """Stored FP32 template spectra = (1/L) sum_m g[m] e^{+2 pi i f m / L} of the
-    oracle's taps (NumPy FFT), to FP32 rounding: as such for the tensor-core
-    filters, in the folded form for the FP32 filter."""
+    oracle's taps (NumPy FFT), to FP32 rounding: in the paired form for the
+    tensor-core filters, in the folded form for the FP32 filter."""
     wl = synth.small_single()
     op = oracle_params(wl)
     p = jerk_params(op, 1 << 16, seg_len=seg_len)
@@ -149,6 +161,8 @@ def test_bank_spectra(pkg, precision, seg_len):
         want = np.fft.ifft(g)          # (1/L) sum_m g[m] e^{+2 pi i f m / L}
         if precision == 0:
             want = fold_spectrum(want, L)
+        else:
+            want = pair_spectrum(want, 64)
         assert np.max(np.abs(bank[row] - want)) < 2e-7 * np.max(np.abs(want)) + 1e-9
     assert len(rows) == 5
 
