@@ -147,6 +147,33 @@ def recorded_traffic(L, alg_bytes, precision=0):
         % (bins, name, small / small_alg, alg_bytes))
 
 
+def recorded_limiter(L, precision=0):
+    """Pipe utilisations of the filter kernel from the committed ncu section
+    capture of the same small case (one launch, 2^16 bins, the full bank), kept
+    in the traffic record beside the DRAM bytes: which unit bounds the kernel.
+    None when the record is missing or was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", TRAFFIC_FILES[precision])
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip()
+    main = "conv.cu" if precision == 0 else "conv_tc.cu"
+    if vals.get("kernel_sha") != kernel_hash(main) or int(vals.get("seg_len", 0)) != L:
+        return None
+    out = {}
+    for k in ("l1tex_throughput_pct", "issue_active_pct", "fma_pipe_pct", "tensor_pipe_pct"):
+        if k in vals:
+            out[k] = float(vals[k])
+    if not out:
+        return None
+    out["source"] = "ncu --set full, one launch at %s bins (profiles/%s)" % (vals.get("bins"), TRAFFIC_FILES[precision])
+    return out
+
+
 # ---------------------------------------------------------------------------
 # clocks
 # ---------------------------------------------------------------------------
@@ -595,6 +622,7 @@ def main():
     roof = {"bound": "alu", "kernel": "conv_kernel (fused FFT-multiply-IFFT-power)",
             "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
             "frac": achieved / peak_alu, "traffic": traffic, "traffic_note": traffic_note,
+            "limiter": recorded_limiter(L, 0),
             "algorithmic_bytes": alg_bytes,
             "flops_per_cell": conv_flops_per_cell(L, V),
             "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (sms, sm_max_mhz),
@@ -622,6 +650,7 @@ def main():
                                              % ("BF16" if a.precision == 1 else "FP16"),
                 "achieved": t_achieved, "peak": t_peak, "unit": "TFLOP/s", "frac": t_achieved / t_peak,
                 "traffic": traffic, "traffic_note": traffic_note, "flops_per_cell": tflops_cell,
+                "limiter": recorded_limiter(L, a.precision),
                 "peak_source": "%s dense bf16 (sustained), FP16 at the same rate" % peaks_src,
                 "alu_view": {"achieved": achieved, "peak": peak_alu, "frac": achieved / peak_alu,
                              "note": "FP32-equivalent transform flops (5 L log2 L + 6 L + 3 V per segment)"}}
