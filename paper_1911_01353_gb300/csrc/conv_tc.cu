@@ -31,6 +31,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "device_sync.cuh"
 #include "fft.cuh"
 #include "jerk_internal.h"
@@ -470,6 +472,15 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
             const RowEntries &en = rent[k & 1];
             const int ne = tq[k & 3].e1 - tq[k & 3].e0;
             const int q0 = seg0 + 1024 * gcol + r;
+            if (ne > 0) {
+                // the rows hold scaled powers (P is not read again)
+#pragma unroll
+                for (int i = 0; i < 16; i += 2) {
+                    const float2 ps = mul2(make_float2(P[i], P[i + 1]), make_float2(psc, psc));
+                    P[i] = ps.x;
+                    P[i + 1] = ps.y;
+                }
+            }
             for (int e = 0; e < ne; ++e) {
                 const int h = en.h[e];
                 float *dst = a.slots + en.off[e];
@@ -477,16 +488,33 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                 if ((h & (h - 1)) == 0) {
                     // h = 1, 2, 4, 8 divides 64: all of this thread's cells are
                     // harmonics of this h, or none is; cell i goes to row
-                    // position quo + i dq (dq = 64 / h) while that is below len
+                    // position quo + i dq (dq = 64 / h) while that is below len.
+                    // The stride is a compile-time constant per h, so the 16
+                    // stores take immediate offsets from one address.
                     const int lh = __ffs(h) - 1, ldq = 6 - lh;
                     if ((q0 & (h - 1)) == 0) {
                         const int quo = q0 >> lh;
                         const int iend = quo >= len ? 0 : min(nvalid, (len - quo + (1 << ldq) - 1) >> ldq);
                         float *d = dst + quo;
+                        auto rows16 = [&](auto ldqc) {
+                            constexpr int LDQ = decltype(ldqc)::value;
+                            if (iend == 16) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            if (i < iend && JERK_CHECK(en.off[e] + quo + (i << ldq) < a.slot_cap, a.chk, kChkTcRowStore))
-                                d[i << ldq] = P[i] * psc;
+                                for (int i = 0; i < 16; ++i)
+                                    if (JERK_CHECK(en.off[e] + quo + (i << LDQ) < a.slot_cap, a.chk, kChkTcRowStore))
+                                        d[i << LDQ] = P[i];
+                            } else {
+#pragma unroll
+                                for (int i = 0; i < 16; ++i)
+                                    if (i < iend &&
+                                        JERK_CHECK(en.off[e] + quo + (i << LDQ) < a.slot_cap, a.chk, kChkTcRowStore))
+                                        d[i << LDQ] = P[i];
+                            }
+                        };
+                        if (h == 1) rows16(std::integral_constant<int, 6>{});
+                        else if (h == 2) rows16(std::integral_constant<int, 5>{});
+                        else if (h == 4) rows16(std::integral_constant<int, 4>{});
+                        else rows16(std::integral_constant<int, 3>{});
                     }
                 } else {
                     // h = 3, 5, 6, 7: quotient and remainder stepped by 64 per cell
@@ -496,7 +524,7 @@ __global__ void __launch_bounds__(THREADS, 1) conv_tc_kernel(ConvArgs a) {
                     for (int i = 0; i < 16; ++i) {
                         if (i < nvalid && rem == 0 && quo < len &&
                             JERK_CHECK(en.off[e] + quo < a.slot_cap, a.chk, kChkTcRowStore))
-                            dst[quo] = P[i] * psc;
+                            dst[quo] = P[i];
                         quo += dq;
                         rem += dr;
                         if (rem >= h) {
