@@ -35,6 +35,7 @@
 #include "fft.cuh"
 #include "jerk_internal.h"
 #include "rows.cuh"
+#include "tmem.cuh"
 
 namespace jerk {
 
@@ -49,6 +50,10 @@ struct ConvCfg {
     static constexpr bool TWS = LOG2L <= 12;                  // twiddles from shared-memory tables
     static constexpr int TWN = TWS ? twiddle_table_elems<LOG2L>() : 0;
     static constexpr int NBUF = LOG2L >= 13 ? 1 : 2;          // template buffers in flight
+    // L = 4096: the inverse transform's twiddles in tensor memory, 64 columns
+    // per thread (warps w, w + 4, .. share a lane range: 4 x 64 columns)
+    static constexpr bool TMT = LOG2L == 12;
+    static constexpr uint32_t TMCOLS = 256;
     // dynamic shared memory: NBUF x template | SEGS x work | twiddle tables |
     // SEGS x staged power row (float) | SEGS x argmax offset within the group (uint16)
     static constexpr size_t SMEM = sizeof(float2) * ((size_t)NBUF * L + (size_t)SEGS * WPAD + (size_t)TWN) +
@@ -65,6 +70,45 @@ __device__ __forceinline__ auto make_tw(const float2 *tab, int j) {
         return tw;
     }
 }
+
+// The inverse transform's twiddles at L = 4096 read from tensor memory: this
+// thread's 64 columns hold, at 0..31, the pass-0 factors w_L^{f1 r} for r =
+// 1..15 in pairs (r, r + 1) as (re, im, re, im) (the last half padding), and
+// at 32..63 the pass-1 factors w_256^{f' r} in the same form: the contents of
+// this thread's entries of the shared-memory tables, copied once per CTA.
+// Each pass reads them 8 columns at a time, the next 8 in flight while the
+// current ones are used.
+struct FftTwTmem {
+    uint32_t ta;   // this thread's first column
+    __device__ __forceinline__ static float2 w(const uint32_t (&r)[8], int q) {
+        return make_float2(__uint_as_float(r[2 * q]), __uint_as_float(r[2 * q + 1]));
+    }
+    __device__ __forceinline__ static void run(uint32_t t, float2 *b) {
+        uint32_t x[8], y[8];
+        tmem_ld8(t, x);
+        tmem_wait_ld8(x);
+        tmem_ld8(t + 8, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[1 + q] = cmul(b[1 + q], w(x, q));
+        tmem_wait_ld8(y);
+        tmem_ld8(t + 16, x);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[5 + q] = cmul(b[5 + q], w(y, q));
+        tmem_wait_ld8(x);
+        tmem_ld8(t + 24, y);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[9 + q] = cmul(b[9 + q], w(x, q));
+        tmem_wait_ld8(y);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) b[13 + q] = cmul(b[13 + q], w(y, q));
+    }
+    template <int R>
+    __device__ __forceinline__ void apply0(float2 *b, int) const {
+        static_assert(R == 16, "tensor-memory twiddles: L = 4096 only");
+        run(ta, b);
+    }
+    __device__ __forceinline__ void applys(float2 *a, int) const { run(ta + 32, a); }
+};
 
 // Bank row (processing index) of position k of a work entry: the identity for
 // whole-bank searches, a lookup when an item searches a sub-grid of the bank.
@@ -101,7 +145,9 @@ conv_kernel(ConvArgs a) {
     __shared__ int sbound[SEGS][JERK_MAX_HARMONIC][2];        // per h: first and last p of the segment
     __shared__ const int64_t *srow[SEGS][2];                  // this segment's row offset / length tables
     __shared__ unsigned long long *sM1[SEGS];                 // this segment's stage-1 max-projection
+    __shared__ uint32_t tslot;                                // tensor-memory base (CC::TMT)
     const SyncNamed bar_half{1 + half, NT};
+    const int warp = tid >> 5;
 
     // (spectrum, template group) entry of this CTA: binary search of the CTA prefix
     int lo = 0, hi = a.n_work - 1;
@@ -143,13 +189,34 @@ conv_kernel(ConvArgs a) {
         tq[half][tb & 3] = TplMeta{t0, __ldg(a.slot_beg + t0), __ldg(a.slot_beg + t0 + 1), 0};
         if (tb + 1 < te) tq[half][(tb + 1) & 3].t = __ldg(a.order + tb + 1);
     }
+    if constexpr (CC::TMT)
+        if (warp == 0) tmem_alloc_warp(smem_u32(&tslot), CC::TMCOLS);
+    tmem_fence_before();
     __syncthreads();
+    tmem_fence_after();
     if (tid == 0)
         for (int b = 0; b < NBUF && tb + b < te; ++b) {
             issued[b] = 1;
             bulk_load(smem + b * L, a.bank + (int64_t)bank_row<ROWS>(a, tb + b) * L, (uint32_t)(L * sizeof(float2)),
                       &full[b]);
         }
+    // this thread's columns: lanes 32 (warp % 4) + lane, columns 64 (warp / 4) ..
+    const uint32_t tcol = CC::TMT ? tslot + ((uint32_t)(32 * (warp & 3)) << 16) + 64u * (uint32_t)(warp >> 2) : 0u;
+    if constexpr (CC::TMT) {
+        // copy this thread's entries of the inverse twiddle tables (pass 0: pairs
+        // k = 0..7 at [k][j]; pass 1: pairs at [k][j mod 16]) into its columns
+        const float4 *p0 = reinterpret_cast<const float4 *>(twtab) + j;
+        const float4 *p1 = reinterpret_cast<const float4 *>(twtab + 16 * C::N0) + (j & 15);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const float4 *src = c < 4 ? p0 + 2 * c * C::N0 : p1 + 2 * (c - 4) * 16;
+            const int step = c < 4 ? C::N0 : 16;
+            const float4 u = src[0], w = src[step];
+            const float x[8] = {u.x, u.y, u.z, u.w, w.x, w.y, w.z, w.w};
+            tmem_st8(tcol + 8 * c, x);
+        }
+        tmem_wait_st();
+    }
 
     // ---- 1. forward FFT of the spread segment -------------------------------
     float2 v[16];
@@ -182,7 +249,10 @@ conv_kernel(ConvArgs a) {
     for (int m = 0; m < 8; ++m) xr[m] = work[j + NT * m];
 
     // ---- 2. templates of this group -----------------------------------------
-    const auto twi = make_tw<LOG2L, +1>(twtab, j);
+    const auto twi = [&] {
+        if constexpr (CC::TMT) return FftTwTmem{tcol};
+        else return make_tw<LOG2L, +1>(twtab, j);
+    }();
     const int rv = fft_rev<LOG2L>(j);
     unsigned vmask = 0;
     // Bit r of vmask: cell r of this thread is valid (within V and the
@@ -391,7 +461,13 @@ conv_kernel(ConvArgs a) {
                            kChkRowStore);
         }
     }
+    tmem_fence_before();
     __syncthreads();
+    if constexpr (CC::TMT)
+        if (warp == 0) {
+            tmem_fence_after();
+            tmem_dealloc_warp(tslot, CC::TMCOLS);
+        }
     if (tid == 0) {
         // never leave with a bulk copy still writing into this CTA's shared memory
         for (int b = 0; b < NBUF; ++b)
