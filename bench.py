@@ -572,8 +572,10 @@ def main():
     torch.cuda.synchronize()
     # FP32 FMA rate and L2 read bandwidth of this GPU (microbenchmarks, outside the timed region)
     f32, l2 = pkg.measure_peaks(local)
-    measured_peaks = {"fp32_fma_tflops": f32, "l2_read_gbs": l2,
-                      "note": "microbenchmarks: independent FMA chains on every SM; 64 MB read 20x from L2"}
+    f32x2 = pkg.measure_packed_fma(local)
+    measured_peaks = {"fp32_fma_tflops": f32, "fp32_packed_fma_tflops": f32x2, "l2_read_gbs": l2,
+                      "note": "microbenchmarks: independent FMA chains on every SM, scalar and packed (f32x2); "
+                              "64 MB read 20x from L2"}
 
     props = torch.cuda.get_device_properties(local)
     bus = None

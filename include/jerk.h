@@ -282,6 +282,17 @@ jerk_status jerk_refine(jerk_plan plan, const void *d_spec, int64_t n, const jer
  * loads, *l2_gbs).  Takes about 100 ms; allocates and frees 64 MB. */
 jerk_status jerk_measure_peaks(int device, double *fp32_tflops, double *l2_gbs);
 
+/* (No counterpart in the paper.)  Measure, on `device`, the FP32 rate of
+ * packed FMAs (fma.rn.f32x2: two lanes per instruction; every SM busy with
+ * independent chains; *tflops counts 4 flops per packed FMA).  The filter
+ * kernels use packed FP32 where their arithmetic pairs up: a packed FMA takes
+ * one issue slot for two scalar FMAs, and this figure shows whether it also
+ * raises the FP32 peak (on GB300 it does not: the roofline keeps the scalar
+ * FMA peak).  Takes about 50 ms; allocates and frees a few MB.  JERK_EINVAL
+ * for a null pointer or a device that does not exist, JERK_ECUDA on a CUDA
+ * error. */
+jerk_status jerk_measure_packed_fma(int device, double *tflops);
+
 /* (No counterpart in the paper.)  Exercise the failure path of the device
  * waits: after the plan's previous work, one GPU thread waits, with the
  * bounded wait the filter kernels use on their bulk copies and tensor-core

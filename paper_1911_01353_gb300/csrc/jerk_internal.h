@@ -169,6 +169,7 @@ cudaError_t launch_finalise_stats(const double *part1, int64_t n1, const double 
 cudaError_t launch_peaks(const PeakArgs &a, int sms, cudaStream_t st);
 cudaError_t launch_wait_check(int *err, uint64_t limit_ns, cudaStream_t st);
 cudaError_t measure_peaks(int sms, double *fp32_tflops, double *l2_gbs);
+cudaError_t measure_packed_fma(int sms, double *tflops);
 
 // host helpers
 int device_sms(int device);         // multiprocessor count of `device` (1 if the query fails)

@@ -493,6 +493,26 @@ __global__ void __launch_bounds__(512) fma_peak_kernel(float *out, int iters, fl
     if (s == 12345.678f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // practically never
 }
 
+// the same FP32 work as packed FMAs (fma.rn.f32x2, two lanes per instruction):
+// 8 independent chains of float2 per thread
+__global__ void __launch_bounds__(512) fma2_peak_kernel(float *out, int iters, float a, float b) {
+    float2 x[8];
+    const float2 a2 = make_float2(a, a), b2 = make_float2(b, b);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = make_float2((float)(threadIdx.x + i) * 1e-3f, (float)i * 1e-3f);
+    for (int k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) x[i] = __ffma2_rn(x[i], a2, b2);
+        }
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i].x + x[i].y;
+    if (s == 12345.678f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;   // practically never
+}
+
 __global__ void __launch_bounds__(256) l2_read_kernel(const float4 *__restrict__ buf, int64_t n4, int reps,
                                                       float *out) {
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -506,6 +526,33 @@ __global__ void __launch_bounds__(256) l2_read_kernel(const float4 *__restrict__
             acc.w += v.w;
         }
     if (acc.x + acc.y + acc.z + acc.w == 12345.678f) out[threadIdx.x] = acc.x;
+}
+
+cudaError_t measure_packed_fma(int sms, double *tflops) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float *scratch = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(float) * 512 * sms * 4);
+    float ms = 0.f;
+    const int blocks = sms * 4, iters = 2048;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first run warms up
+        cudaEventRecord(e0, st);
+        fma2_peak_kernel<<<blocks, 512, 0, st>>>(scratch, iters, 0.999f, 1e-4f);
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    }
+    // 4 flops per packed FMA (two lanes, two flops each)
+    if (e == cudaSuccess) *tflops = 4.0 * 8 * 16 * (double)iters * blocks * 512 / (ms * 1e-3) / 1e12;
+    if (e == cudaSuccess) e = cudaGetLastError();
+    cudaFree(scratch);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    return e;
 }
 
 int device_sms(int device) {

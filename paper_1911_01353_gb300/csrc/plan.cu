@@ -1434,6 +1434,17 @@ jerk_status jerk_measure_peaks(int device, double *fp32_tflops, double *l2_gbs) 
     return JERK_OK;
 }
 
+jerk_status jerk_measure_packed_fma(int device, double *tflops) {
+    if (!tflops) return JERK_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return JERK_EINVAL;
+    JCHECK(cudaSetDevice(device));
+    int sms = 0;
+    JCHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    JCHECK(measure_packed_fma(sms, tflops));
+    return JERK_OK;
+}
+
 jerk_status jerk_check_waits(jerk_plan pl, int32_t limit_us, void *stream) {
     if (!pl || limit_us < 1 || limit_us > 1000000) return JERK_EINVAL;
     JCHECK(cudaSetDevice(pl->device));

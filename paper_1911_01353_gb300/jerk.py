@@ -27,8 +27,8 @@ EXPORTS = ("jerk_plan_create", "jerk_templates", "jerk_search", "jerk_search_hos
            "jerk_normalise", "jerk_taps", "jerk_plane", "jerk_maxproj", "jerk_stats",
            "jerk_profile", "jerk_phase_times", "jerk_peaks_noalloc", "jerk_template_row",
            "jerk_search_batch_grid", "jerk_plan_share", "jerk_power_at", "jerk_refine", "jerk_check_waits",
-           "jerk_measure_peaks", "jerk_check_counts", "jerk_check_inject", "jerk_params_validate", "jerk_search_range",
-           "jerk_range_sums", "jerk_select", "jerk_subharmonic")
+           "jerk_measure_peaks", "jerk_measure_packed_fma", "jerk_check_counts", "jerk_check_inject",
+           "jerk_params_validate", "jerk_search_range", "jerk_range_sums", "jerk_select", "jerk_subharmonic")
 PHASES = ("normalise", "conv", "harmonic", "stats", "peaks")
 
 
@@ -121,6 +121,7 @@ def lib() -> ctypes.CDLL:
             "jerk_check_waits": ([vp, i32, vp], st),
             "jerk_measure_peaks": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                    st),
+            "jerk_measure_packed_fma": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double)], st),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -135,6 +136,13 @@ def measure_peaks(device: int = 0):
     f, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().jerk_measure_peaks(device, ctypes.byref(f), ctypes.byref(b)), "jerk_measure_peaks")
     return f.value, b.value
+
+
+def measure_packed_fma(device: int = 0):
+    """FP32 TFLOP/s of packed (f32x2) FMAs measured on `device` (jerk_measure_packed_fma)."""
+    f = ctypes.c_double()
+    _check(lib().jerk_measure_packed_fma(device, ctypes.byref(f)), "jerk_measure_packed_fma")
+    return f.value
 
 
 class JerkError(RuntimeError):
