@@ -456,3 +456,18 @@ def test_candidate_overflow_reports_true_count(pkg):
         assert e.value.code == jerk.JERK_EOVERFLOW
     res = oracle.search(F, op)
     assert len(res.candidates) > 16
+
+
+# ---------------------------------------------------------------------------
+# roofline denominators
+# ---------------------------------------------------------------------------
+
+def test_packed_fma_rate_equals_scalar(pkg):
+    """Packed (f32x2) FMAs run at the scalar FMA rate: the filters use them to
+    save issue slots, and their FP32 roofline keeps the scalar peak as its
+    denominator.  A packed rate near twice the scalar one would make that
+    denominator wrong, and this test fails then."""
+    f32, l2 = pkg.measure_peaks(0)
+    f32x2 = pkg.measure_packed_fma(0)
+    assert f32 > 0 and l2 > 0 and f32x2 > 0
+    assert 0.8 < f32x2 / f32 < 1.25, (f32, f32x2)
