@@ -14,7 +14,10 @@
 //      (sums and twiddled differences of its two spectrum halves): the
 //      segment's spectrum repeats with period L/2, so the transform's first
 //      pass splits into two half-size DFTs and each thread keeps only 8
-//      spectrum values;
+//      spectrum values.  The butterflies act on the (re, im) pair of each
+//      value with packed FP32 (fft.cuh); at L = 4096 the inverse transform's
+//      twiddles come from tensor memory, where each thread keeps its own
+//      (tmem.cuh), not from the shared-memory tables;
 //   3. epilogue in registers: running (max, argmax) per cell over the group
 //      -> one packed 64-bit atomicMax per cell into the stage-1
 //      max-projection; statistics (SIGMA mode); the harmonic rows the
